@@ -1,0 +1,229 @@
+"""FP64 CPU oracle for the stochastic Barnes-Hut hot path (Madan et al., SIGGRAPH 2025).
+
+TEST INFRASTRUCTURE. Only the test suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
+baseline leg import this package. The CUDA library never does, and this package imports nothing
+from it: the two are independent restatements of the paper.
+
+The arithmetic lives in ``sbh_oracle.c`` (plain C, FP64 sums, FP32 decisions, OpenMP over
+queries); this module compiles it with the host C compiler and marshals numpy arrays.
+
+Functions and the passages they follow:
+  brute(...)        Eq. 1, the exact kernel sum.
+  Tree(...)         Sec. 3.1, the octree-like tree with aggregate mass and centre of mass.
+  Tree.bh(...)      Algorithm 1 (Barnes-Hut), Eq. 2.
+  Tree.replay(...)  Algorithm 2 with Eq. 5 (Russian roulette), Eq. 6 (swap), Eq. 7 (estimator),
+                    driven by the same counter-based Philox4x32-10 stream as the GPU kernel.
+  Tree.enumerate()  exact mean and variance of Eq. 7 by enumeration (Appendix A).
+  philox(...)       Philox4x32-10 (Salmon et al., SC'11).
+
+Parity pins (tests/test_oracle_*.py): closed forms for the brute force, hand-built trees,
+enumeration == brute force (the theorem), zero variance for an affine kernel, replay statistics
+against the enumerated distribution, Philox against an independent implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sbh_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+COULOMB, WINDING, SMOOTHDIST, AFFINE = 0, 1, 2, 3
+SAMPLE_MASS, SAMPLE_COUNT = 0, 1
+RR_PAPER, RR_OFF, RR_HALF = 0, 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile sbh_oracle.c into liboracle.so next to it (gcc, OpenMP, no FP contraction)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-fvisibility=hidden", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Kernel(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("softening", C.c_double), ("alpha", C.c_double),
+                ("affine", C.c_double * 3)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("sampling", C.c_int32), ("rr", C.c_int32), ("coherent", C.c_int32),
+                ("pad", C.c_int32)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build())
+        P = C.c_void_p
+        i64, i32, u64 = C.c_int64, C.c_int32, C.c_uint64
+        lib.sbho_philox4x32_10.argtypes = [P, P, P]
+        lib.sbho_brute.argtypes = [C.POINTER(_Kernel), P, P, P, i64, P, i64, P]
+        lib.sbho_tree_build.argtypes = [P, P, P, i64, i32, i32]
+        lib.sbho_tree_build.restype = P
+        lib.sbho_tree_free.argtypes = [P]
+        lib.sbho_tree_nnodes.argtypes = [P]
+        lib.sbho_tree_nnodes.restype = i64
+        lib.sbho_tree_meta.argtypes = [P, P, P]
+        lib.sbho_tree_export.argtypes = [P] + [P] * 11
+        lib.sbho_bh.argtypes = [P, C.POINTER(_Kernel), P, i64, C.c_float, P]
+        lib.sbho_replay.argtypes = [P, C.POINTER(_Kernel), P, i64, i32, u64, C.POINTER(_Opts), P, P]
+        lib.sbho_enumerate.argtypes = [P, C.POINTER(_Kernel), P, i64, C.POINTER(_Opts), P, P]
+        lib.sbho_max_threads.restype = i32
+        lib.sbho_set_threads.argtypes = [i32]
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f32(a, cols=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    if cols is not None:
+        a = a.reshape(-1, cols)
+    return a
+
+
+def kernel(kind: int, softening: float = 1e-3, alpha: float = 200.0, affine=(0.0, 0.0, 0.0)) -> _Kernel:
+    k = _Kernel()
+    k.kind = int(kind)
+    k.softening = float(softening)
+    k.alpha = float(alpha)
+    for i in range(3):
+        k.affine[i] = float(affine[i])
+    return k
+
+
+def _opts(sampling=SAMPLE_MASS, rr=RR_PAPER, coherent=False) -> _Opts:
+    o = _Opts()
+    o.sampling, o.rr, o.coherent, o.pad = int(sampling), int(rr), int(bool(coherent)), 0
+    return o
+
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x32-10 of one counter block (4 x u32) under a key (2 x u32)."""
+    lib = _load()
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    out = np.zeros(4, dtype=np.uint32)
+    lib.sbho_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+def brute(points, weights, queries, kind=COULOMB, normals=None, softening=1e-3, alpha=200.0,
+          affine=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Eq. 1: F(q) = sum_i m_i f(p_i, q), FP64 with compensated summation. For the smooth
+    distance kernel this is the sum of exponentials (take -log(F)/alpha for the distance)."""
+    lib = _load()
+    pts, w, q = _f32(points, 3), _f32(weights), _f32(queries, 3)
+    nrm = _f32(normals, 3)
+    out = np.zeros(q.shape[0], dtype=np.float64)
+    k = kernel(kind, softening, alpha, affine)
+    lib.sbho_brute(C.byref(k), _ptr(pts), _ptr(w), _ptr(nrm), pts.shape[0], _ptr(q), q.shape[0], _ptr(out))
+    return out
+
+
+class Tree:
+    """The oracle's tree over (points, weights[, normals]) with per-dimension branching d."""
+
+    def __init__(self, points, weights, normals=None, leaf_size: int = 1, d: int = 4):
+        lib = _load()
+        self.points = _f32(points, 3)
+        self.weights = _f32(weights)
+        self.normals = _f32(normals, 3)
+        self.n = self.points.shape[0]
+        self.d = d
+        h = lib.sbho_tree_build(_ptr(self.points), _ptr(self.weights), _ptr(self.normals), self.n,
+                                int(leaf_size), int(d))
+        if not h:
+            raise ValueError("oracle tree build rejected its inputs")
+        self._h = h
+        self._lib = lib
+        self.n_nodes = int(lib.sbho_tree_nnodes(h))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            self._lib.sbho_tree_free(h)
+            self._h = None
+
+    def meta(self) -> dict:
+        m = np.zeros(5, dtype=np.float32)
+        ids = np.zeros(2, dtype=np.int64)
+        self._lib.sbho_tree_meta(self._h, _ptr(m), _ptr(ids))
+        return {"lo": m[:3].copy(), "side": float(m[3]), "diam0": float(m[4]),
+                "first_sub": int(ids[0]), "n_sub": int(ids[1])}
+
+    def export(self) -> dict:
+        n, N = self.n, self.n_nodes
+        a = {
+            "perm": np.zeros(n, np.int64), "code": np.zeros(n, np.uint64),
+            "begin": np.zeros(N, np.int64), "end": np.zeros(N, np.int64),
+            "first_child": np.zeros(N, np.int64), "nchild": np.zeros(N, np.int32),
+            "level": np.zeros(N, np.int32), "mass": np.zeros(N, np.float64),
+            "com": np.zeros((N, 3), np.float64), "dip": np.zeros((N, 3), np.float64),
+            "cdf": np.zeros(N, np.float32),
+        }
+        self._lib.sbho_tree_export(self._h, *[_ptr(a[k]) for k in
+                                              ("perm", "code", "begin", "end", "first_child", "nchild",
+                                               "level", "mass", "com", "dip", "cdf")])
+        return a
+
+    def bh(self, queries, beta: float, kind=COULOMB, softening=1e-3, alpha=200.0,
+           affine=(0.0, 0.0, 0.0)) -> np.ndarray:
+        """Algorithm 1 for every query; beta = inf gives the exact sum."""
+        q = _f32(queries, 3)
+        out = np.zeros(q.shape[0], np.float64)
+        k = kernel(kind, softening, alpha, affine)
+        self._lib.sbho_bh(self._h, C.byref(k), _ptr(q), q.shape[0], C.c_float(beta), _ptr(out))
+        return out
+
+    def replay(self, queries, S: int = 1, seed: int = 0, kind=COULOMB, softening=1e-3, alpha=200.0,
+               affine=(0.0, 0.0, 0.0), sampling=SAMPLE_MASS, rr=RR_PAPER, coherent=False,
+               return_swaps=False):
+        """Algorithm 2 replayed with the Philox stream; returns the FP64 estimate of the kernel
+        sum per query (the sum of exponentials for the smooth distance kernel)."""
+        q = _f32(queries, 3)
+        out = np.zeros(q.shape[0], np.float64)
+        swaps = np.zeros(q.shape[0], np.int64)
+        k = kernel(kind, softening, alpha, affine)
+        o = _opts(sampling, rr, coherent)
+        self._lib.sbho_replay(self._h, C.byref(k), _ptr(q), q.shape[0], int(S), C.c_uint64(seed & (2**64 - 1)),
+                              C.byref(o), _ptr(out), _ptr(swaps))
+        return (out, swaps) if return_swaps else out
+
+    def enumerate(self, queries, kind=COULOMB, softening=1e-3, alpha=200.0, affine=(0.0, 0.0, 0.0),
+                  sampling=SAMPLE_MASS, rr=RR_PAPER):
+        """Exact (mean, variance) of the one-sample estimator per query, by enumeration."""
+        q = _f32(queries, 3)
+        mean = np.zeros(q.shape[0], np.float64)
+        var = np.zeros(q.shape[0], np.float64)
+        k = kernel(kind, softening, alpha, affine)
+        o = _opts(sampling, rr, False)
+        self._lib.sbho_enumerate(self._h, C.byref(k), _ptr(q), q.shape[0], C.byref(o), _ptr(mean), _ptr(var))
+        return mean, var
+
+
+def max_threads() -> int:
+    return int(_load().sbho_max_threads())
+
+
+def set_threads(n: int) -> None:
+    _load().sbho_set_threads(int(n))

@@ -1,0 +1,696 @@
+/*
+ * sbh_oracle.c -- the plain, slow, FP64 CPU oracle for the stochastic Barnes-Hut hot path
+ * (Madan, Sharp, Williams, Museth, Levin: "Stochastic Barnes-Hut Approximation for Fast
+ * Summation on the GPU", SIGGRAPH 2025).
+ *
+ * THIS IS TEST INFRASTRUCTURE. Only the test suite, the smoke check and the benchmark's CPU
+ * baseline leg load it. It shares no code, header, table or helper with the CUDA library: the
+ * two are written independently from the paper, and the only thing they have in common is the
+ * seeded input generator that feeds both.
+ *
+ * What it computes, each function citing the passage it follows:
+ *   - brute-force kernel sum F(q) = sum_i m_i f(p_i, q)                     (Sec. 3, Eq. 1)
+ *   - the octree-like tree with per-dimension branching d (2 or 4), node aggregate mass and
+ *     centre of mass (Sec. 3.1), built from its plain recursive definition
+ *   - Barnes-Hut, Algorithm 1 (Sec. 3.1, Eq. 2; supplemental "Pseudocode")
+ *   - a replay of the stratified path estimator, Algorithm 2, with Russian roulette Eq. 5,
+ *     contribution swap Eq. 6 and the one-path estimator Eq. 7 (Sec. 3.3, 3.3.1)
+ *   - the exact mean and variance of that estimator by enumerating every outcome of the path
+ *     sampler on small trees: the operational form of the unbiasedness proof (Appendix A).
+ *
+ * Precision. Sums, kernel values and estimator weights are FP64. The decisions that turn a
+ * floating-point value into a discrete choice -- the Morton quantisation of a point, the child a
+ * path steps into, and the Russian-roulette continue/stop -- are taken in FP32, the precision the
+ * paper states for its implementation (Sec. 4.1), with every operation a single IEEE
+ * round-to-nearest step (this file must be compiled with -ffp-contract=off), so that the GPU
+ * kernels can reproduce them bit for bit.
+ *
+ * Readings where the paper is silent (each is also listed in the design notes):
+ *   - |B_a| is the diagonal of the node's octree cell, sqrt(3) * side * d^-level.
+ *   - A node whose points all fall in one child cell is replaced by that child (single-child
+ *     chains collapse); the kept node keeps its own level.
+ *   - A node is a leaf when it holds <= leaf_size points or sits at the deepest level; a leaf
+ *     with more than one point has its points as children, one level deeper.
+ *   - The path index I is drawn lazily, one child per level, child c of T with probability
+ *     m_c / m_T (or |T_c| / |T| for the paper's count-uniform choice), which gives
+ *     p(I in T_{I,k}) = m_{I,k} / m_a exactly as drawing I up front with p(I=i) = m_i / m_a.
+ *   - Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = (seed low 32,
+ *     seed high 32), counter = (query index, subdomain index, sample index, depth k); word 0
+ *     picks the child, word 1 drives Russian roulette; u = (x >> 8) * 2^-24.
+ *   - Child pick: the stored FP32 prefix fraction cdf_c = (sum_{c'<=c} m_c') / m_T (the last
+ *     child's is exactly 1); the chosen child is the number of children c < last with
+ *     cdf_c <= u.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+#define SBHO_API __attribute__((visibility("default")))
+
+enum { K_COULOMB = 0, K_WINDING = 1, K_SMOOTHDIST = 2, K_AFFINE = 3 };
+enum { SAMPLE_MASS = 0, SAMPLE_COUNT = 1 };
+enum { RR_PAPER = 0, RR_OFF = 1, RR_HALF = 2 };
+
+/* ------------------------------------------------------------------------------------------ */
+/* Philox4x32-10, from its published definition (Salmon et al., SC'11, Sec. 4 and Table 2):     */
+/* ten rounds of two 32x32->64 multiplies with Feistel-style mixing; the key is bumped by the   */
+/* Weyl constants (golden ratio, sqrt(3)-1) before every round but the first.                  */
+/* ------------------------------------------------------------------------------------------ */
+SBHO_API void sbho_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t mul0 = 0xD2511F53u, mul1 = 0xCD9E8D57u;
+    const uint32_t weyl0 = 0x9E3779B9u, weyl1 = 0xBB67AE85u;
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += weyl0; k1 += weyl1; }
+        uint64_t prod0 = (uint64_t)mul0 * (uint64_t)x0;
+        uint64_t prod1 = (uint64_t)mul1 * (uint64_t)x2;
+        uint32_t hi0 = (uint32_t)(prod0 >> 32), lo0 = (uint32_t)prod0;
+        uint32_t hi1 = (uint32_t)(prod1 >> 32), lo1 = (uint32_t)prod1;
+        uint32_t y0 = hi1 ^ x1 ^ k0;
+        uint32_t y1 = lo1;
+        uint32_t y2 = hi0 ^ x3 ^ k1;
+        uint32_t y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* uniform in [0,1) with 24 random bits: exactly representable in FP32 and FP64 */
+static float unit24f(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+/* ------------------------------------------------------------------------------------------ */
+/* Kernels f(p, q) times the source weight, in FP64 (Sec. 3 Eq. 1; Sec. 4.2 Coulomb-like       */
+/* potential; Sec. 4.3.2 winding numbers; Sec. 4.3.3 smooth distance).                        */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int32_t kind;
+    double softening;  /* Coulomb: f = 1 / sqrt(r^2 + eps^2) */
+    double alpha;      /* smooth distance: f = exp(-alpha r) */
+    double affine[3];  /* test kernel: f = 1 + g . (p - q), affine in p */
+} sbho_kernel;
+
+/* weight * f(p, q); dip is the node's dipole sum_j m_j n_j (used by the winding kernel only) */
+static double term(const sbho_kernel *k, const double p[3], double m, const double dip[3],
+                   const double q[3])
+{
+    double dx = p[0] - q[0], dy = p[1] - q[1], dz = p[2] - q[2];
+    double r2 = dx * dx + dy * dy + dz * dz;
+    switch (k->kind) {
+    case K_COULOMB:
+        return m / sqrt(r2 + k->softening * k->softening);
+    case K_WINDING: {
+        if (r2 == 0.0) return 0.0;
+        double r = sqrt(r2);
+        return (dx * dip[0] + dy * dip[1] + dz * dip[2]) / (4.0 * M_PI * r2 * r);
+    }
+    case K_SMOOTHDIST:
+        return m * exp(-k->alpha * sqrt(r2));
+    case K_AFFINE:
+        return m * (1.0 + k->affine[0] * dx + k->affine[1] * dy + k->affine[2] * dz);
+    }
+    return 0.0;
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Brute force, Eq. 1: F(q) = sum_i m_i f(p_i, q). Neumaier-compensated FP64 summation.        */
+/* ------------------------------------------------------------------------------------------ */
+static double point_term(const sbho_kernel *k, const float *pts, const float *w, const float *nrm,
+                         int64_t i, const double q[3])
+{
+    double p[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
+    double m = w[i];
+    double dip[3] = {0, 0, 0};
+    if (nrm) {
+        dip[0] = m * (double)nrm[3 * i];
+        dip[1] = m * (double)nrm[3 * i + 1];
+        dip[2] = m * (double)nrm[3 * i + 2];
+    }
+    return term(k, p, m, dip, q);
+}
+
+SBHO_API void sbho_brute(const sbho_kernel *k, const float *pts, const float *w, const float *nrm,
+                         int64_t n, const float *queries, int64_t nq, double *out)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < nq; ++j) {
+        double q[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
+        double sum = 0.0, comp = 0.0;
+        for (int64_t i = 0; i < n; ++i) {
+            double t = point_term(k, pts, w, nrm, i, q);
+            double s = sum + t;
+            if (fabs(sum) >= fabs(t)) comp += (sum - s) + t;
+            else comp += (t - s) + sum;
+            sum = s;
+        }
+        out[j] = sum + comp;
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* The tree (Sec. 3.1): an octree-like subdivision of the root cube with per-dimension         */
+/* branching d; every node stores its point set (a range of the Morton-sorted points), its     */
+/* aggregate mass m_a = sum m_b and centre of mass p_a = sum m_b p_b / m_a.                     */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n;
+    int32_t d;          /* per-dimension branching: 2 or 4 */
+    int32_t bits;       /* Morton bits per level: log2(d^3) = 3 or 6 */
+    int32_t max_level;  /* 20 (d=2) or 10 (d=4): 60-bit codes */
+    int32_t leaf_size;
+    int32_t has_normals;
+    float lo[3], side, diam0;  /* root cube corner and edge; cell diagonal at level 0 (FP32) */
+    int64_t *perm;   /* [n] original index of the i-th point in Morton order */
+    uint64_t *code;  /* [n] sorted Morton codes */
+    int64_t n_nodes;
+    int64_t *begin, *end, *first_child, *parent;
+    int32_t *nchild, *level;
+    double *mass, *com, *dip;      /* FP64 aggregates: [N], [3N], [3N] */
+    float *mass32, *com32, *cdf;   /* FP32 roundings used by the FP32 decisions: [N], [3N], [N] */
+    int64_t n_sub;                 /* subdomains (Sec. 3.3.1): the root's children, or the root */
+    int64_t first_sub;
+} otree;
+
+/* Quantise one coordinate to a 20-bit cell index: floor((x - lo) * (2^20 / side)), clamped.
+ * FP32, one rounding per operation, no contraction. */
+static uint32_t quant20(float x, float lo, float scale)
+{
+    float t = (x - lo) * scale;
+    float f = floorf(t);
+    uint32_t c = (f <= 0.0f) ? 0u : (uint32_t)f;
+    return c > 1048575u ? 1048575u : c;
+}
+
+/* Morton interleave, x bit first within each (x, y, z) triple, most significant triple first */
+static uint64_t morton60(uint32_t cx, uint32_t cy, uint32_t cz)
+{
+    uint64_t code = 0;
+    for (int b = 19; b >= 0; --b) {
+        code = (code << 3) | ((uint64_t)((cx >> b) & 1u) << 2) | ((uint64_t)((cy >> b) & 1u) << 1) |
+               (uint64_t)((cz >> b) & 1u);
+    }
+    return code;
+}
+
+typedef struct { uint64_t code; int64_t idx; } keyed;
+static int cmp_keyed(const void *a, const void *b)
+{
+    const keyed *x = (const keyed *)a, *y = (const keyed *)b;
+    if (x->code != y->code) return x->code < y->code ? -1 : 1;
+    return (x->idx > y->idx) - (x->idx < y->idx);  /* ties keep the input order */
+}
+
+/* child cell digit of code at level (1-based): the bits-wide group below level-1 */
+static uint32_t digit_at(const otree *t, uint64_t code, int level)
+{
+    int shift = 60 - t->bits * level;
+    return (uint32_t)((code >> shift) & ((1u << t->bits) - 1u));
+}
+
+/* A node under construction, before breadth-first numbering */
+typedef struct tnode {
+    int64_t begin, end;
+    int32_t level;
+    int32_t nchild;
+    struct tnode **child;
+} tnode;
+
+static tnode *new_tnode(int64_t b, int64_t e, int level)
+{
+    tnode *x = (tnode *)calloc(1, sizeof(tnode));
+    x->begin = b; x->end = e; x->level = level;
+    return x;
+}
+
+/* Points [b, e) as children of a multi-point leaf, one level below it */
+static void attach_points(tnode *x)
+{
+    int64_t cnt = x->end - x->begin;
+    x->nchild = (int32_t)cnt;
+    x->child = (tnode **)calloc((size_t)cnt, sizeof(tnode *));
+    for (int64_t i = 0; i < cnt; ++i) x->child[i] = new_tnode(x->begin + i, x->begin + i + 1, x->level + 1);
+}
+
+/* The node holding the points [b, e), which first appear as one run at `level`. */
+static tnode *make_node(const otree *t, int64_t b, int64_t e, int level)
+{
+    tnode *x = new_tnode(b, e, level);
+    int64_t cnt = e - b;
+    if (cnt == 1) return x;                                   /* a source point */
+    if (cnt <= t->leaf_size) { attach_points(x); return x; }  /* small leaf */
+    for (;;) {
+        if (x->level == t->max_level) { attach_points(x); return x; }  /* deepest level */
+        /* split into runs of equal digits one level down */
+        int runs = 1;
+        for (int64_t i = b + 1; i < e; ++i)
+            if (digit_at(t, t->code[i], x->level + 1) != digit_at(t, t->code[i - 1], x->level + 1)) ++runs;
+        if (runs == 1) { x->level += 1; continue; }  /* single child: collapse into it */
+        x->nchild = runs;
+        x->child = (tnode **)calloc((size_t)runs, sizeof(tnode *));
+        int64_t s = b; int c = 0;
+        for (int64_t i = b + 1; i <= e; ++i) {
+            if (i == e || digit_at(t, t->code[i], x->level + 1) != digit_at(t, t->code[i - 1], x->level + 1)) {
+                x->child[c++] = make_node(t, s, i, x->level + 1);
+                s = i;
+            }
+        }
+        return x;
+    }
+}
+
+static void free_tnode(tnode *x)
+{
+    for (int i = 0; i < x->nchild; ++i) free_tnode(x->child[i]);
+    free(x->child);
+    free(x);
+}
+
+static int64_t count_tnodes(const tnode *x)
+{
+    int64_t c = 1;
+    for (int i = 0; i < x->nchild; ++i) c += count_tnodes(x->child[i]);
+    return c;
+}
+
+SBHO_API void *sbho_tree_build(const float *pts, const float *w, const float *nrm, int64_t n,
+                               int32_t leaf_size, int32_t d)
+{
+    if (n < 1 || leaf_size < 1 || (d != 2 && d != 4)) return NULL;
+    otree *t = (otree *)calloc(1, sizeof(otree));
+    t->n = n; t->d = d; t->bits = (d == 4) ? 6 : 3; t->max_level = 60 / t->bits;
+    t->leaf_size = leaf_size; t->has_normals = nrm != NULL;
+
+    /* root cube: lower corner = per-axis minimum, edge = largest extent (1 if all coincide) */
+    float mn[3], mx[3];
+    for (int a = 0; a < 3; ++a) { mn[a] = pts[a]; mx[a] = pts[a]; }
+    for (int64_t i = 1; i < n; ++i)
+        for (int a = 0; a < 3; ++a) {
+            float v = pts[3 * i + a];
+            if (v < mn[a]) mn[a] = v;
+            if (v > mx[a]) mx[a] = v;
+        }
+    float side = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        float ext = mx[a] - mn[a];
+        if (ext > side) side = ext;
+        t->lo[a] = mn[a];
+    }
+    if (side == 0.0f) side = 1.0f;
+    t->side = side;
+    t->diam0 = 1.7320508075688772f * side;
+    float scale = 1048576.0f / side;
+
+    keyed *kv = (keyed *)malloc((size_t)n * sizeof(keyed));
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t cx = quant20(pts[3 * i], t->lo[0], scale);
+        uint32_t cy = quant20(pts[3 * i + 1], t->lo[1], scale);
+        uint32_t cz = quant20(pts[3 * i + 2], t->lo[2], scale);
+        kv[i].code = morton60(cx, cy, cz);
+        kv[i].idx = i;
+    }
+    qsort(kv, (size_t)n, sizeof(keyed), cmp_keyed);
+    t->perm = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    t->code = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
+    for (int64_t i = 0; i < n; ++i) { t->perm[i] = kv[i].idx; t->code[i] = kv[i].code; }
+    free(kv);
+
+    tnode *root = make_node(t, 0, n, 0);
+    int64_t N = count_tnodes(root);
+    t->n_nodes = N;
+    t->begin = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    t->end = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    t->first_child = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    t->parent = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    t->nchild = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    t->level = (int32_t *)malloc((size_t)N * sizeof(int32_t));
+    t->mass = (double *)calloc((size_t)N, sizeof(double));
+    t->com = (double *)calloc((size_t)N * 3, sizeof(double));
+    t->dip = (double *)calloc((size_t)N * 3, sizeof(double));
+    t->mass32 = (float *)malloc((size_t)N * sizeof(float));
+    t->com32 = (float *)malloc((size_t)N * 3 * sizeof(float));
+    t->cdf = (float *)malloc((size_t)N * sizeof(float));
+
+    /* breadth-first numbering: the children of a node get consecutive indices, in Morton order */
+    tnode **queue = (tnode **)malloc((size_t)N * sizeof(tnode *));
+    int64_t head = 0, tail = 0;
+    queue[tail++] = root;
+    t->parent[0] = -1;
+    while (head < tail) {
+        int64_t id = head;
+        tnode *x = queue[head++];
+        t->begin[id] = x->begin; t->end[id] = x->end; t->level[id] = x->level;
+        t->nchild[id] = x->nchild;
+        t->first_child[id] = x->nchild ? tail : -1;
+        for (int c = 0; c < x->nchild; ++c) {
+            t->parent[tail] = id;
+            queue[tail++] = x->child[c];
+        }
+    }
+    free(queue);
+    free_tnode(root);
+
+    /* aggregates (Sec. 3.1): direct FP64 sums over each node's points */
+    for (int64_t v = 0; v < N; ++v) {
+        double m = 0, s[3] = {0, 0, 0}, nd[3] = {0, 0, 0};
+        for (int64_t i = t->begin[v]; i < t->end[v]; ++i) {
+            int64_t j = t->perm[i];
+            double mj = w[j];
+            m += mj;
+            for (int a = 0; a < 3; ++a) s[a] += mj * (double)pts[3 * j + a];
+            if (nrm)
+                for (int a = 0; a < 3; ++a) nd[a] += mj * (double)nrm[3 * j + a];
+        }
+        t->mass[v] = m;
+        for (int a = 0; a < 3; ++a) {
+            t->com[3 * v + a] = s[a] / m;
+            t->dip[3 * v + a] = nd[a];
+            t->com32[3 * v + a] = (float)t->com[3 * v + a];
+        }
+        t->mass32[v] = (float)m;
+    }
+    /* child-pick prefix fractions within each parent */
+    t->cdf[0] = 1.0f;
+    for (int64_t v = 0; v < N; ++v) {
+        int nc = t->nchild[v];
+        if (!nc) continue;
+        int64_t fc = t->first_child[v];
+        double tot = 0;
+        for (int c = 0; c < nc; ++c) tot += t->mass[fc + c];
+        double pre = 0;
+        for (int c = 0; c < nc; ++c) {
+            pre += t->mass[fc + c];
+            t->cdf[fc + c] = (c == nc - 1) ? 1.0f : (float)(pre / tot);
+        }
+    }
+    if (t->nchild[0] > 0) { t->first_sub = t->first_child[0]; t->n_sub = t->nchild[0]; }
+    else { t->first_sub = 0; t->n_sub = 1; }
+    return t;
+}
+
+SBHO_API void sbho_tree_free(void *h)
+{
+    otree *t = (otree *)h;
+    if (!t) return;
+    free(t->perm); free(t->code); free(t->begin); free(t->end); free(t->first_child);
+    free(t->parent); free(t->nchild); free(t->level); free(t->mass); free(t->com); free(t->dip);
+    free(t->mass32); free(t->com32); free(t->cdf);
+    free(t);
+}
+
+SBHO_API int64_t sbho_tree_nnodes(const void *h) { return ((const otree *)h)->n_nodes; }
+
+/* Root cube and subdomains: meta = {lo.x, lo.y, lo.z, side, diam0}; ids = {first_sub, n_sub} */
+SBHO_API void sbho_tree_meta(const void *h, float meta[5], int64_t ids[2])
+{
+    const otree *t = (const otree *)h;
+    meta[0] = t->lo[0]; meta[1] = t->lo[1]; meta[2] = t->lo[2]; meta[3] = t->side; meta[4] = t->diam0;
+    ids[0] = t->first_sub; ids[1] = t->n_sub;
+}
+
+/* Copy the tree out (any pointer may be NULL). Arrays are [n] or [n_nodes] (x3 for vectors). */
+SBHO_API void sbho_tree_export(const void *h, int64_t *perm, uint64_t *code, int64_t *begin,
+                               int64_t *end, int64_t *first_child, int32_t *nchild, int32_t *level,
+                               double *mass, double *com, double *dip, float *cdf)
+{
+    const otree *t = (const otree *)h;
+    size_t N = (size_t)t->n_nodes, n = (size_t)t->n;
+    if (perm) memcpy(perm, t->perm, n * sizeof(int64_t));
+    if (code) memcpy(code, t->code, n * sizeof(uint64_t));
+    if (begin) memcpy(begin, t->begin, N * sizeof(int64_t));
+    if (end) memcpy(end, t->end, N * sizeof(int64_t));
+    if (first_child) memcpy(first_child, t->first_child, N * sizeof(int64_t));
+    if (nchild) memcpy(nchild, t->nchild, N * sizeof(int32_t));
+    if (level) memcpy(level, t->level, N * sizeof(int32_t));
+    if (mass) memcpy(mass, t->mass, N * sizeof(double));
+    if (com) memcpy(com, t->com, 3 * N * sizeof(double));
+    if (dip) memcpy(dip, t->dip, 3 * N * sizeof(double));
+    if (cdf) memcpy(cdf, t->cdf, N * sizeof(float));
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Per-node quantities shared by Barnes-Hut and the estimator                                   */
+/* ------------------------------------------------------------------------------------------ */
+static double node_term(const otree *t, const sbho_kernel *k, int64_t v, const double q[3])
+{
+    return term(k, &t->com[3 * v], t->mass[v], &t->dip[3 * v], q);
+}
+
+/* |B_a|: the cell diagonal at the node's level, in FP32 (scaling by a power of two is exact) */
+static float diam32(const otree *t, int level)
+{
+    return ldexpf(t->diam0, -(t->bits / 3) * level);
+}
+
+/* ||q - p_a|| in FP32 with a fixed operation order: ((dx*dx + dy*dy) + dz*dz), then sqrt */
+static float dist32(const float p[3], const float q[3])
+{
+    float dx = p[0] - q[0], dy = p[1] - q[1], dz = p[2] - q[2];
+    float s = dx * dx + dy * dy;
+    s = s + dz * dz;
+    return sqrtf(s);
+}
+
+/* far-field ratio beta~ = ||q - p_a|| / |B_a| (Sec. 3.3), FP32 */
+static float ffratio32(const otree *t, int64_t v, const float q[3])
+{
+    return dist32(&t->com32[3 * v], q) / diam32(t, t->level[v]);
+}
+
+/* Russian-roulette continue probability into child c of node v, Eq. 5, in FP32 */
+static float rr_prob32(const otree *t, int64_t v, int64_t c, const float q[3], int rr)
+{
+    if (rr == RR_OFF) return 1.0f;
+    if (rr == RR_HALF) return 0.5f;
+    float bt = ffratio32(t, v, q);
+    float bc = ffratio32(t, c, q);
+    float num = bt > 1.0f ? bt : 1.0f;
+    float r = num / bc;  /* bc == 0 gives +inf, hence probability 1 */
+    return r < 1.0f ? r : 1.0f;
+}
+
+/* Eq. 5 in exact arithmetic (FP64), used by the enumeration */
+static double rr_prob64(const otree *t, int64_t v, int64_t c, const double q[3], int rr)
+{
+    if (rr == RR_OFF) return 1.0;
+    if (rr == RR_HALF) return 0.5;
+    double dv = 0, dc = 0;
+    for (int a = 0; a < 3; ++a) {
+        double x = t->com[3 * v + a] - q[a], y = t->com[3 * c + a] - q[a];
+        dv += x * x; dc += y * y;
+    }
+    double bt = sqrt(dv) / ldexp(sqrt(3.0) * t->side, -(t->bits / 3) * t->level[v]);
+    double bc = sqrt(dc) / ldexp(sqrt(3.0) * t->side, -(t->bits / 3) * t->level[c]);
+    double num = bt > 1.0 ? bt : 1.0;
+    if (bc == 0.0) return 1.0;
+    double r = num / bc;
+    return r < 1.0 ? r : 1.0;
+}
+
+/* Child of v containing the path index (lazy draw). Mass: count the stored prefix fractions
+ * cdf_c <= u among all but the last child. Count: the child holding the floor(u * |T|)-th point. */
+static int64_t pick_child(const otree *t, int64_t v, uint32_t x, int sampling)
+{
+    int64_t fc = t->first_child[v];
+    int nc = t->nchild[v];
+    if (sampling == SAMPLE_COUNT) {
+        int64_t cnt = t->end[v] - t->begin[v];
+        int64_t target = t->begin[v] + (int64_t)(((uint64_t)(x >> 8) * (uint64_t)cnt) >> 24);
+        int64_t c = 0;
+        while (c + 1 < nc && t->begin[fc + c + 1] <= target) ++c;
+        return fc + c;
+    }
+    float u = unit24f(x);
+    int64_t c = 0;
+    for (int j = 0; j < nc - 1; ++j)
+        if (t->cdf[fc + j] <= u) ++c;
+    return fc + c;
+}
+
+/* p(I in T_v) for a path rooted at subdomain a */
+static double p_in(const otree *t, int64_t v, int64_t a, int sampling)
+{
+    if (sampling == SAMPLE_COUNT)
+        return (double)(t->end[v] - t->begin[v]) / (double)(t->end[a] - t->begin[a]);
+    return t->mass[v] / t->mass[a];
+}
+
+/* Contribution swap, Eq. 6: sum over children of m_c f(p_c, q), minus m_v f(p_v, q) */
+static double swap_delta(const otree *t, const sbho_kernel *k, int64_t v, const double q[3])
+{
+    double s = 0;
+    for (int c = 0; c < t->nchild[v]; ++c) s += node_term(t, k, t->first_child[v] + c, q);
+    return s - node_term(t, k, v, q);
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Barnes-Hut, Algorithm 1: stop at a leaf or when beta~ >= beta, else recurse into children.   */
+/* The far-field test is taken in FP32 (beta~ as above); sums are FP64.                        */
+/* ------------------------------------------------------------------------------------------ */
+static double bh_rec(const otree *t, const sbho_kernel *k, int64_t v, const double q[3],
+                     const float q32[3], float beta)
+{
+    if (t->nchild[v] == 0 || ffratio32(t, v, q32) >= beta) return node_term(t, k, v, q);
+    double F = 0;
+    for (int c = 0; c < t->nchild[v]; ++c) F += bh_rec(t, k, t->first_child[v] + c, q, q32, beta);
+    return F;
+}
+
+SBHO_API void sbho_bh(const void *h, const sbho_kernel *k, const float *queries, int64_t nq,
+                      float beta, double *out)
+{
+    const otree *t = (const otree *)h;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < nq; ++j) {
+        float q32[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
+        double q[3] = {q32[0], q32[1], q32[2]};
+        out[j] = bh_rec(t, k, 0, q, q32, beta);
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Algorithm 2 (stratified path sample estimator), replayed with the Philox stream.             */
+/*   for each subdomain a (children of the root, Sec. 3.3.1):                                  */
+/*     CV_a = m_a f(p_a, q);  F_a = 0                                                          */
+/*     for s in 1..S: T = a, k = 0, p_rr = 1                                                   */
+/*       while T is not a leaf:                                                                */
+/*         c   = child of T containing I            (drawn lazily, word 0)                     */
+/*         p   = Eq. 5 for (T, c)                   (FP32)                                     */
+/*         if rand >= p: stop                       (word 1)                                   */
+/*         Delta = Eq. 6 at T;  p_agg = p(I in T);  p_rr *= p                                  */
+/*         F_a += Delta / (p_agg p_rr);  T = c;  k += 1                                        */
+/*     F += CV_a + F_a / S                                                                     */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct {
+    int32_t sampling;   /* SAMPLE_MASS (default) or SAMPLE_COUNT (the paper's uniform index) */
+    int32_t rr;         /* RR_PAPER (Eq. 5), RR_OFF, RR_HALF */
+    int32_t coherent;   /* 1: every query uses query index 0 in the counter */
+    int32_t pad;
+} sbho_opts;
+
+SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *queries, int64_t nq,
+                          int32_t S, uint64_t seed, const sbho_opts *opts, double *out,
+                          int64_t *nswaps)
+{
+    const otree *t = (const otree *)h;
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const int sampling = opts ? opts->sampling : SAMPLE_MASS;
+    const int rr = opts ? opts->rr : RR_PAPER;
+    const int coherent = opts ? opts->coherent : 0;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < nq; ++j) {
+        float q32[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
+        double q[3] = {q32[0], q32[1], q32[2]};
+        double F = 0;
+        int64_t swaps = 0;
+        for (int64_t ai = 0; ai < t->n_sub; ++ai) {
+            int64_t a = t->first_sub + ai;
+            double CV = node_term(t, k, a, q);
+            double Fa = 0;
+            for (int32_t s = 0; s < S; ++s) {
+                int64_t T = a;
+                uint32_t depth = 0;
+                double prr = 1.0;
+                while (t->nchild[T] > 0) {
+                    uint32_t ctr[4] = {coherent ? 0u : (uint32_t)j, (uint32_t)ai, (uint32_t)s, depth};
+                    uint32_t x[4];
+                    sbho_philox4x32_10(ctr, key, x);
+                    int64_t c = pick_child(t, T, x[0], sampling);
+                    float p = rr_prob32(t, T, c, q32, rr);
+                    if (unit24f(x[1]) >= p) break;
+                    double delta = swap_delta(t, k, T, q);
+                    double pagg = p_in(t, T, a, sampling);
+                    prr *= (double)p;
+                    Fa += delta / (pagg * prr);
+                    ++swaps;
+                    T = c;
+                    ++depth;
+                }
+            }
+            F += CV + Fa / (double)S;
+        }
+        out[j] = F;
+        if (nswaps) nswaps[j] = swaps;
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Exact mean and variance of the one-sample estimator (S = 1) by enumerating every outcome    */
+/* of the sampler: at node T reached with probability P and running estimate V, each child c   */
+/* is taken with probability pi_c and continued with probability p (Eq. 5); stopping ends the  */
+/* path with value V, continuing adds Delta_T / (p_agg p_rr). This is the sum the proof of the */
+/* theorem (Appendix A) rearranges. Subdomains are independent, so variances add.             */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct { double e1, e2; } moments;
+
+static void enum_rec(const otree *t, const sbho_kernel *k, int64_t a, int64_t T, const double q[3],
+                     double P, double V, double prr, int sampling, int rr, moments *acc)
+{
+    if (t->nchild[T] == 0) { acc->e1 += P * V; acc->e2 += P * V * V; return; }
+    double delta = swap_delta(t, k, T, q);
+    double pagg = p_in(t, T, a, sampling);
+    int64_t fc = t->first_child[T];
+    double tot = 0;
+    for (int c = 0; c < t->nchild[T]; ++c)
+        tot += (sampling == SAMPLE_COUNT) ? (double)(t->end[fc + c] - t->begin[fc + c]) : t->mass[fc + c];
+    for (int c = 0; c < t->nchild[T]; ++c) {
+        int64_t ch = fc + c;
+        double w = (sampling == SAMPLE_COUNT) ? (double)(t->end[ch] - t->begin[ch]) : t->mass[ch];
+        double pi = w / tot;
+        double p = rr_prob64(t, T, ch, q, rr);
+        double Pstop = P * pi * (1.0 - p);
+        acc->e1 += Pstop * V;
+        acc->e2 += Pstop * V * V;
+        double prr2 = prr * p;
+        enum_rec(t, k, a, ch, q, P * pi * p, V + delta / (pagg * prr2), prr2, sampling, rr, acc);
+    }
+}
+
+/* mean[j] = E[F_1(q_j)], var[j] = Var[F_1(q_j)] */
+SBHO_API void sbho_enumerate(const void *h, const sbho_kernel *k, const float *queries, int64_t nq,
+                             const sbho_opts *opts, double *mean, double *var)
+{
+    const otree *t = (const otree *)h;
+    const int sampling = opts ? opts->sampling : SAMPLE_MASS;
+    const int rr = opts ? opts->rr : RR_PAPER;
+    for (int64_t j = 0; j < nq; ++j) {
+        double q[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
+        double E = 0, Var = 0;
+        for (int64_t ai = 0; ai < t->n_sub; ++ai) {
+            int64_t a = t->first_sub + ai;
+            moments m = {0, 0};
+            enum_rec(t, k, a, a, q, 1.0, 0.0, 1.0, sampling, rr, &m);
+            E += node_term(t, k, a, q) + m.e1;
+            Var += m.e2 - m.e1 * m.e1;
+        }
+        mean[j] = E;
+        var[j] = Var;
+    }
+}
+
+/* thread control for the timed CPU baseline */
+SBHO_API int32_t sbho_max_threads(void)
+{
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+SBHO_API void sbho_set_threads(int32_t n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
