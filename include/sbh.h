@@ -1,0 +1,177 @@
+/*
+ * sbh.h -- C ABI of the GB300 stochastic Barnes-Hut library (libsbh.so).
+ *
+ * The library evaluates kernel sums F(q) = sum_i m_i f(p_i, q) over a source point set for many
+ * query points (Madan, Sharp, Williams, Museth, Levin, "Stochastic Barnes-Hut Approximation for
+ * Fast Summation on the GPU", SIGGRAPH 2025, Sec. 3, Eq. 1), with
+ *   - sbh_build:       the octree-like tree with aggregate mass and centre of mass (Sec. 3.1),
+ *                      built on the GPU from Morton codes;
+ *   - sbh_eval:        the stratified, unbiased path estimator (Sec. 3.3, Eq. 5-7, Algorithm 2);
+ *   - sbh_eval_bh:     deterministic Barnes-Hut (Sec. 3.1, Eq. 2, Algorithm 1), the GPU baseline;
+ *   - sbh_eval_brute:  the exact sum by tiled brute force (Eq. 1).
+ *
+ * Conventions shared by every entry point:
+ *   - Buffers are caller-owned, contiguous, C order, FP32 unless stated. Points and queries are
+ *     [n][3] (x, y, z interleaved). "device" buffers must be device (or managed) memory of the
+ *     current CUDA device; nothing is read from or written to host memory unless stated.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream). Work is enqueued on it and
+ *     the call returns without synchronising, except where a call says it synchronises.
+ *   - Every call returns an sbh_status; nothing throws across the ABI. On failure
+ *     sbh_last_error() returns a message for the calling thread, and output buffers are left in
+ *     an unspecified state.
+ *   - Results are bitwise reproducible for the same inputs, seed and device.
+ */
+#ifndef SBH_H
+#define SBH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SBH_VERSION 1
+
+#if defined(__GNUC__)
+#define SBH_API __attribute__((visibility("default")))
+#else
+#define SBH_API
+#endif
+
+typedef enum {
+    SBH_OK = 0,
+    SBH_EINVAL = 1,       /* an argument is out of its documented range */
+    SBH_ENOMEM = 2,       /* device memory could not be allocated */
+    SBH_ECUDA = 3,        /* a CUDA runtime call failed; see sbh_last_error() */
+    SBH_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
+    SBH_EUNSUPPORTED = 5  /* the request needs something this tree or device does not have */
+} sbh_status;
+
+/* Kernel f(p, q) of the sum (Sec. 4.2, 4.3). Each source contributes m_i f(p_i, q):
+ *   SBH_COULOMB     f = 1 / sqrt(|p - q|^2 + softening^2)              (Sec. 4.2, sign +)
+ *   SBH_WINDING     m f = m ((p - q) . n) / (4 pi |p - q|^3), 0 at p = q (Sec. 4.3.2); a node
+ *                   uses its dipole sum_j m_j n_j at its centre of mass. Needs normals.
+ *   SBH_SMOOTHDIST  f = exp(-alpha |p - q|); the output is the smooth distance
+ *                   -log(F) / alpha (Sec. 4.3.3), +inf where the estimate of F is <= 0.
+ *   SBH_AFFINE      f = 1 + g . (p - q) with g = affine[0..2]: a test kernel, affine in p, for
+ *                   which every contribution swap is zero and the estimator is exact. */
+typedef enum { SBH_COULOMB = 0, SBH_WINDING = 1, SBH_SMOOTHDIST = 2, SBH_AFFINE = 3 } sbh_kernel_kind;
+
+typedef struct {
+    int32_t kind;       /* sbh_kernel_kind */
+    float softening;    /* SBH_COULOMB: epsilon >= 0 */
+    float alpha;        /* SBH_SMOOTHDIST: alpha > 0 */
+    float affine[3];    /* SBH_AFFINE: g */
+} sbh_kernel;
+
+/* Estimator options. Pass NULL for the defaults (all zero). */
+typedef struct {
+    int32_t sampling;   /* 0: child picked with probability m_c / m_T (aggregate mass);
+                           1: |T_c| / |T| (uniform path index, the paper's Algorithm 2) */
+    int32_t rr;         /* 0: Eq. 5; 1: no Russian roulette (p = 1); 2: fixed p = 1/2 */
+    int32_t seed_mode;  /* 0: random stream keyed by query index; 1: every query uses index 0
+                           (coherent across queries, the paper's identical per-warp seeding) */
+    int32_t reserved;   /* must be 0 */
+} sbh_eval_opts;
+
+typedef struct sbh_tree sbh_tree;  /* opaque, library-owned */
+
+/* Tree summary, filled by sbh_tree_info (host memory). `which`: 0 = the 64-ary tree used by the
+ * estimator (per-dimension branching d = 4), 1 = the 8-ary tree used by Barnes-Hut (d = 2). */
+typedef struct {
+    int64_t n_points;
+    int64_t n_nodes;
+    int32_t leaf_size;
+    int32_t has_normals;
+    int32_t max_depth;       /* number of node generations below the root */
+    int32_t reserved;
+    int64_t first_sub;       /* subdomains (Sec. 3.3.1): node ids [first_sub, first_sub + n_sub) */
+    int64_t n_sub;
+    float lo[3];             /* root cube lower corner */
+    float side;              /* root cube edge */
+    float diam0;             /* |B| of the root cell: sqrt(3) * side, FP32 */
+    float reserved_f;
+} sbh_tree_meta;
+
+/* Host copy of one tree for inspection. Every pointer may be NULL (skipped); arrays hold
+ * n_points or n_nodes entries (x4 / x3 where stated). Node ids are breadth-first: the children
+ * of node v are first_child[v] .. first_child[v] + nchild[v] - 1, in Morton order. */
+typedef struct {
+    int32_t* perm;         /* [n_points] input index of the i-th point in Morton order */
+    uint64_t* code;        /* [n_points] sorted 60-bit Morton codes */
+    int32_t* begin;        /* [n_nodes] first sorted point of the node */
+    int32_t* end;          /* [n_nodes] one past the last sorted point */
+    int32_t* first_child;  /* [n_nodes] -1 for a source point */
+    int32_t* nchild;       /* [n_nodes] 0 for a source point */
+    int32_t* level;        /* [n_nodes] cell level (|B| = diam0 * d^-level) */
+    int32_t* parent;       /* [n_nodes] -1 for the root */
+    float* com_mass;       /* [n_nodes][4] centre of mass x, y, z and aggregate mass (FP32) */
+    double* com_mass64;    /* [n_nodes][4] the same in FP64, before rounding */
+    float* dipole;         /* [n_nodes][3] sum_j m_j n_j (zeros without normals) */
+    float* cdf;            /* [n_nodes] prefix fraction of the node's mass among its siblings */
+} sbh_tree_export_buffers;
+
+/* Build the tree over n sources (Sec. 3.1).
+ *   points   device [n][3]   finite
+ *   weights  device [n]      masses m_i > 0 and finite (the child pick divides by them)
+ *   normals  device [n][3] or NULL; required by SBH_WINDING evaluations
+ *   n        1 <= n <= 2^28
+ *   leaf_size 1 <= leaf_size <= 64: nodes with at most this many points are leaves
+ * Builds the 64-ary estimator tree now; the 8-ary Barnes-Hut tree is built from the same sorted
+ * codes on the first sbh_eval_bh call. The input buffers are not retained. On success *out owns
+ * device memory until sbh_tree_free. Validation of the inputs synchronises the stream once; the
+ * build itself is enqueued on `stream` and the call synchronises once more at its end. Returns
+ * SBH_EINVAL for a bad size, NaN/Inf coordinates or a non-positive weight, SBH_ENOMEM when
+ * device memory runs out, SBH_EUNSUPPORTED when more than 2^24 - 1 points share one cell of the
+ * deepest level (2^-20 of the root cube per axis). */
+SBH_API sbh_status sbh_build(const float* points, const float* weights, const float* normals, int64_t n,
+                     int32_t leaf_size, void* stream, sbh_tree** out);
+
+/* Stochastic estimate of F at nq queries (Algorithm 2 with Eq. 5-7; Sec. 3.3.1 subdomains are
+ * the root's children), S = samples_per_subdomain >= 1 paths per subdomain, random stream
+ * Philox4x32-10 keyed by `seed` and counted by (query index, subdomain, sample, depth).
+ *   queries device [nq][3]; out device [nq]: the estimate of F (the smooth distance for
+ *   SBH_SMOOTHDIST). nq = 0 is a no-op. SBH_EINVAL if the kernel is SBH_WINDING and the tree
+ *   has no normals, or if an option is out of range. */
+SBH_API sbh_status sbh_eval(const sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel,
+                    int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
+                    float* out, void* stream);
+
+/* Deterministic Barnes-Hut (Algorithm 1) on the 8-ary tree: a node is used whole when it is a
+ * single point or ||q - p_a|| / |B_a| >= beta = 1 / theta (theta = 0 gives the exact sum).
+ * warp_vote = 1 takes the decision jointly for the 32 queries of a warp (a node is opened when
+ * any of them needs it); 0 decides per query, exactly as Algorithm 1. The first call builds the
+ * 8-ary tree (enqueued on `stream`). */
+SBH_API sbh_status sbh_eval_bh(sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel,
+                       float theta, int32_t warp_vote, float* out, void* stream);
+
+/* Exact sum (Eq. 1) by tiled brute force: every query against every source.
+ *   points/weights/normals as in sbh_build (normals may be NULL unless SBH_WINDING);
+ *   fp64_accum = 1 accumulates each tile's FP32 partial sum in FP64 (the error reference),
+ *   0 keeps everything in FP32. out device [nq]. */
+SBH_API sbh_status sbh_eval_brute(const float* points, const float* weights, const float* normals, int64_t n,
+                          const float* queries, int64_t nq, sbh_kernel kernel, int32_t fp64_accum,
+                          float* out, void* stream);
+
+/* Tree summary (host struct). Synchronises the tree's build stream. which: 0 or 1 (see above);
+ * SBH_EUNSUPPORTED when the 8-ary tree has not been built yet. */
+SBH_API sbh_status sbh_tree_info(const sbh_tree* tree, int32_t which, sbh_tree_meta* meta);
+
+/* Copy a tree to host buffers sized from sbh_tree_info. Synchronises. */
+SBH_API sbh_status sbh_tree_export(const sbh_tree* tree, int32_t which, const sbh_tree_export_buffers* buf);
+
+/* Release the tree's device memory (NULL is a no-op). Synchronises the tree's build stream. */
+SBH_API void sbh_tree_free(sbh_tree* tree);
+
+/* Message describing the calling thread's most recent failure ("" if none). */
+SBH_API const char* sbh_last_error(void);
+
+/* SBH_VERSION of the loaded library. */
+SBH_API int32_t sbh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SBH_H */

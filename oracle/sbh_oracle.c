@@ -558,6 +558,7 @@ SBHO_API void sbho_bh(const void *h, const sbho_kernel *k, const float *queries,
 
 /* ------------------------------------------------------------------------------------------ */
 /* Algorithm 2 (stratified path sample estimator), replayed with the Philox stream.             */
+/* The counter's query index is qidx[j] when given (queries drawn from a larger set), else j.  */
 /*   for each subdomain a (children of the root, Sec. 3.3.1):                                  */
 /*     CV_a = m_a f(p_a, q);  F_a = 0                                                          */
 /*     for s in 1..S: T = a, k = 0, p_rr = 1                                                   */
@@ -577,8 +578,8 @@ typedef struct {
 } sbho_opts;
 
 SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *queries, int64_t nq,
-                          int32_t S, uint64_t seed, const sbho_opts *opts, double *out,
-                          int64_t *nswaps)
+                          int32_t S, uint64_t seed, const sbho_opts *opts, const uint32_t *qidx,
+                          double *out, int64_t *nswaps)
 {
     const otree *t = (const otree *)h;
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
@@ -600,7 +601,7 @@ SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *quer
                 uint32_t depth = 0;
                 double prr = 1.0;
                 while (t->nchild[T] > 0) {
-                    uint32_t ctr[4] = {coherent ? 0u : (uint32_t)j, (uint32_t)ai, (uint32_t)s, depth};
+                    uint32_t ctr[4] = {coherent ? 0u : (qidx ? qidx[j] : (uint32_t)j), (uint32_t)ai, (uint32_t)s, depth};
                     uint32_t x[4];
                     sbho_philox4x32_10(ctr, key, x);
                     int64_t c = pick_child(t, T, x[0], sampling);

@@ -1,0 +1,256 @@
+"""Stochastic Barnes-Hut on GB300: Python binding of libsbh.so (include/sbh.h).
+
+Madan, Sharp, Williams, Museth, Levin, "Stochastic Barnes-Hut Approximation for Fast Summation on
+the GPU" (SIGGRAPH 2025): the unbiased path estimator of kernel sums F(q) = sum_i m_i f(p_i, q)
+that uses the Barnes-Hut level-of-detail hierarchy as a control variate (Sec. 3.3, Algorithm 2).
+
+Every function here only marshals arguments: the work runs in the CUDA kernels of libsbh.so.
+There is no CPU fallback; if the library has not been built, loading it raises.
+
+    tree = sbh_build(points, weights, normals=None, leaf_size=1)       # Sec. 3.1, on the GPU
+    F    = sbh_eval(tree, queries, kernel="coulomb", samples_per_subdomain=1, seed=0)
+    Fbh  = sbh_eval_bh(tree, queries, kernel="coulomb", theta=0.5)      # Algorithm 1
+    Fex  = sbh_eval_brute(points, weights, queries, kernel="coulomb")   # Eq. 1
+
+Tensors are float32, contiguous, on the current CUDA device; points and queries are [n, 3].
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+__all__ = ["SBHError", "Tree", "EvalOpts", "kernel", "load_library", "sbh_build", "sbh_eval", "sbh_eval_bh",
+           "sbh_eval_brute", "sbh_tree_info", "sbh_tree_export", "sbh_tree_free", "sbh_last_error", "sbh_version",
+           "KERNELS"]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libsbh.so")
+
+KERNELS = {"coulomb": 0, "winding": 1, "smoothdist": 2, "affine": 3}
+_STATUS = {0: "SBH_OK", 1: "SBH_EINVAL", 2: "SBH_ENOMEM", 3: "SBH_ECUDA", 4: "SBH_ETIMEOUT", 5: "SBH_EUNSUPPORTED"}
+
+
+class SBHError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Kernel(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("softening", C.c_float), ("alpha", C.c_float), ("affine", C.c_float * 3)]
+
+
+class EvalOpts(C.Structure):
+    """sbh_eval_opts: sampling (0 mass, 1 count), rr (0 Eq. 5, 1 off, 2 half), seed_mode (0, 1)."""
+    _fields_ = [("sampling", C.c_int32), ("rr", C.c_int32), ("seed_mode", C.c_int32), ("reserved", C.c_int32)]
+
+
+class _Meta(C.Structure):
+    _fields_ = [("n_points", C.c_int64), ("n_nodes", C.c_int64), ("leaf_size", C.c_int32),
+                ("has_normals", C.c_int32), ("max_depth", C.c_int32), ("reserved", C.c_int32),
+                ("first_sub", C.c_int64), ("n_sub", C.c_int64), ("lo", C.c_float * 3), ("side", C.c_float),
+                ("diam0", C.c_float), ("reserved_f", C.c_float)]
+
+
+class _Export(C.Structure):
+    _fields_ = [(name, C.c_void_p) for name in ("perm", "code", "begin", "end", "first_child", "nchild", "level",
+                                                 "parent", "com_mass", "com_mass64", "dipole", "cdf")]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library():
+    """Load libsbh.so from the package directory; raise if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; "
+                               "g.build()'` (there is no CPU fallback)")
+        lib = C.CDLL(LIB_PATH)
+        P, i64, i32 = C.c_void_p, C.c_int64, C.c_int32
+        lib.sbh_version.restype = i32
+        lib.sbh_last_error.restype = C.c_char_p
+        lib.sbh_build.argtypes = [P, P, P, i64, i32, P, C.POINTER(P)]
+        lib.sbh_eval.argtypes = [P, P, i64, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts), P, P]
+        lib.sbh_eval_bh.argtypes = [P, P, i64, _Kernel, C.c_float, i32, P, P]
+        lib.sbh_eval_brute.argtypes = [P, P, P, i64, P, i64, _Kernel, i32, P, P]
+        lib.sbh_tree_info.argtypes = [P, i32, C.POINTER(_Meta)]
+        lib.sbh_tree_export.argtypes = [P, i32, C.POINTER(_Export)]
+        lib.sbh_tree_free.argtypes = [P]
+        lib.sbh_tree_free.restype = None
+        for f in ("sbh_build", "sbh_eval", "sbh_eval_bh", "sbh_eval_brute", "sbh_tree_info", "sbh_tree_export"):
+            getattr(lib, f).restype = i32
+        _lib = lib
+        return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise SBHError(status, load_library().sbh_last_error().decode(errors="replace"))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev(t, name, cols=None, allow_none=False):
+    """Validate a float32 contiguous CUDA tensor (no silent copies) and return its pointer."""
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous float32")
+    if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+        raise ValueError(f"{name} must have shape [n, {cols}]")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def kernel(kind="coulomb", softening: float = 1e-3, alpha: float = 200.0, affine=(0.0, 0.0, 0.0)) -> _Kernel:
+    """sbh_kernel for a kind name ("coulomb", "winding", "smoothdist", "affine") or number."""
+    k = _Kernel()
+    k.kind = KERNELS[kind] if isinstance(kind, str) else int(kind)
+    k.softening = float(softening)
+    k.alpha = float(alpha)
+    for i in range(3):
+        k.affine[i] = float(affine[i])
+    return k
+
+
+class Tree:
+    """Owner of an sbh_tree handle; freed with the object (or sbh_tree_free)."""
+
+    def __init__(self, handle: int, n: int, has_normals: bool):
+        self._h = C.c_void_p(handle)
+        self.n = n
+        self.has_normals = has_normals
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            load_library().sbh_tree_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sbh_version() -> int:
+    return int(load_library().sbh_version())
+
+
+def sbh_last_error() -> str:
+    return load_library().sbh_last_error().decode(errors="replace")
+
+
+def sbh_build(points, weights, normals=None, leaf_size: int = 1, stream=None) -> Tree:
+    """Build the tree (Sec. 3.1) over points [n, 3], weights [n] (> 0), optional normals [n, 3]."""
+    lib = load_library()
+    n = int(points.shape[0]) if points is not None else 0
+    h = C.c_void_p()
+    _check(lib.sbh_build(_dev(points, "points", 3), _dev(weights, "weights"),
+                         _dev(normals, "normals", 3, allow_none=True), n, int(leaf_size), _stream(stream),
+                         C.byref(h)))
+    return Tree(h.value, n, normals is not None)
+
+
+def _kernel_arg(kind, softening, alpha, affine):
+    return kind if isinstance(kind, _Kernel) else kernel(kind, softening, alpha, affine)
+
+
+def sbh_eval(tree: Tree, queries, kernel="coulomb", samples_per_subdomain: int = 1, seed: int = 0,
+             opts: EvalOpts | None = None, out=None, stream=None, softening: float = 1e-3, alpha: float = 200.0,
+             affine=(0.0, 0.0, 0.0)):
+    """Stochastic estimate (Algorithm 2) at queries [nq, 3]; returns out [nq]."""
+    torch = _torch()
+    lib = load_library()
+    nq = int(queries.shape[0])
+    if out is None:
+        out = torch.empty(nq, dtype=torch.float32, device=queries.device)
+    k = _kernel_arg(kernel, softening, alpha, affine)
+    _check(lib.sbh_eval(tree.handle, _dev(queries, "queries", 3), nq, k, int(samples_per_subdomain),
+                        C.c_uint64(int(seed) & (2**64 - 1)), C.byref(opts) if opts is not None else None,
+                        _dev(out, "out"), _stream(stream)))
+    return out
+
+
+def sbh_eval_bh(tree: Tree, queries, kernel="coulomb", theta: float = 0.5, warp_vote: bool = True, out=None,
+                stream=None, softening: float = 1e-3, alpha: float = 200.0, affine=(0.0, 0.0, 0.0)):
+    """Deterministic Barnes-Hut (Algorithm 1) with beta = 1 / theta; returns out [nq]."""
+    torch = _torch()
+    lib = load_library()
+    nq = int(queries.shape[0])
+    if out is None:
+        out = torch.empty(nq, dtype=torch.float32, device=queries.device)
+    k = _kernel_arg(kernel, softening, alpha, affine)
+    _check(lib.sbh_eval_bh(tree.handle, _dev(queries, "queries", 3), nq, k, C.c_float(theta), int(bool(warp_vote)),
+                           _dev(out, "out"), _stream(stream)))
+    return out
+
+
+def sbh_eval_brute(points, weights, queries, kernel="coulomb", normals=None, fp64_accum: bool = True, out=None,
+                   stream=None, softening: float = 1e-3, alpha: float = 200.0, affine=(0.0, 0.0, 0.0)):
+    """Exact sum (Eq. 1) by tiled brute force; returns out [nq]."""
+    torch = _torch()
+    lib = load_library()
+    nq = int(queries.shape[0])
+    n = int(points.shape[0])
+    if out is None:
+        out = torch.empty(nq, dtype=torch.float32, device=queries.device)
+    k = _kernel_arg(kernel, softening, alpha, affine)
+    _check(lib.sbh_eval_brute(_dev(points, "points", 3), _dev(weights, "weights"),
+                              _dev(normals, "normals", 3, allow_none=True), n, _dev(queries, "queries", 3), nq, k,
+                              int(bool(fp64_accum)), _dev(out, "out"), _stream(stream)))
+    return out
+
+
+def sbh_tree_info(tree: Tree, which: int = 0) -> dict:
+    m = _Meta()
+    _check(load_library().sbh_tree_info(tree.handle, int(which), C.byref(m)))
+    return {"n_points": m.n_points, "n_nodes": m.n_nodes, "leaf_size": m.leaf_size, "has_normals": bool(m.has_normals),
+            "max_depth": m.max_depth, "first_sub": m.first_sub, "n_sub": m.n_sub, "lo": np.array(m.lo[:], np.float32),
+            "side": m.side, "diam0": m.diam0}
+
+
+def sbh_tree_export(tree: Tree, which: int = 0) -> dict:
+    """Host copy of a tree: numpy arrays keyed like sbh_tree_export_buffers."""
+    info = sbh_tree_info(tree, which)
+    n, N = info["n_points"], info["n_nodes"]
+    a = {"perm": np.zeros(n, np.int32), "code": np.zeros(n, np.uint64), "begin": np.zeros(N, np.int32),
+         "end": np.zeros(N, np.int32), "first_child": np.zeros(N, np.int32), "nchild": np.zeros(N, np.int32),
+         "level": np.zeros(N, np.int32), "parent": np.zeros(N, np.int32), "com_mass": np.zeros((N, 4), np.float32),
+         "com_mass64": np.zeros((N, 4), np.float64), "dipole": np.zeros((N, 3), np.float32),
+         "cdf": np.zeros(N, np.float32)}
+    e = _Export()
+    for name, arr in a.items():
+        setattr(e, name, arr.ctypes.data_as(C.c_void_p))
+    _check(load_library().sbh_tree_export(tree.handle, int(which), C.byref(e)))
+    a["info"] = info
+    return a
+
+
+def sbh_tree_free(tree: Tree) -> None:
+    tree.free()

@@ -1,0 +1,311 @@
+// sbh_api.cu -- the extern "C" entry points declared in include/sbh.h: argument checks, error
+// reporting, ownership of the tree object, and dispatch to the build and evaluation kernels.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+
+#include "sbh.h"
+#include "sbh_build.cuh"
+#include "sbh_eval.cuh"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+sbh_status fail(sbh_status st, const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+sbh_status cuda_fail(cudaError_t e, const char* what)
+{
+    const sbh_status st = (e == cudaErrorMemoryAllocation) ? SBH_ENOMEM : SBH_ECUDA;
+    return fail(st, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+// nonzero if p is usable from the current device (device or managed memory)
+bool device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+sbh_status check_kernel(const sbh_kernel& k, sbh::KernelParams* kp)
+{
+    if (k.kind < SBH_COULOMB || k.kind > SBH_AFFINE) return fail(SBH_EINVAL, "unknown kernel kind %d", (int)k.kind);
+    if (k.kind == SBH_COULOMB && !(k.softening >= 0.0f && isfinite(k.softening)))
+        return fail(SBH_EINVAL, "softening must be finite and >= 0");
+    if (k.kind == SBH_SMOOTHDIST && !(k.alpha > 0.0f && isfinite(k.alpha)))
+        return fail(SBH_EINVAL, "alpha must be finite and > 0");
+    kp->kind = k.kind;
+    kp->eps2 = k.softening * k.softening;
+    kp->alpha = k.alpha;
+    for (int i = 0; i < 3; ++i) kp->g[i] = k.affine[i];
+    return SBH_OK;
+}
+
+void release(sbh_tree* T, cudaStream_t s)
+{
+    sbh::free_tree(T->t4, s);
+    sbh::free_tree(T->t2, s);
+    sbh::dfree(T->code, s);
+    sbh::dfree(T->perm, s);
+    sbh::dfree(T->spw, s);
+    sbh::dfree(T->snrm, s);
+    sbh::dfree(T->lcp4, s);
+    sbh::dfree(T->lcp2, s);
+    cudaStreamSynchronize(s);
+    delete T;
+}
+
+constexpr int64_t kMaxPoints = (int64_t)1 << 28;
+
+}  // namespace
+
+extern "C" {
+
+int32_t sbh_version(void) { return SBH_VERSION; }
+
+const char* sbh_last_error(void) { return g_err; }
+
+sbh_status sbh_build(const float* points, const float* weights, const float* normals, int64_t n, int32_t leaf_size,
+                     void* stream, sbh_tree** out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(SBH_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > kMaxPoints) return fail(SBH_EINVAL, "n = %lld outside [1, 2^28]", (long long)n);
+    if (leaf_size < 1 || leaf_size > sbh::kMaxLeafSize)
+        return fail(SBH_EINVAL, "leaf_size = %d outside [1, %d]", (int)leaf_size, sbh::kMaxLeafSize);
+    if (!device_ptr(points) || !device_ptr(weights))
+        return fail(SBH_EINVAL, "points and weights must be device memory");
+    if (normals && !device_ptr(normals)) return fail(SBH_EINVAL, "normals must be device memory or NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    sbh_tree* T = new (std::nothrow) sbh_tree();
+    if (!T) return fail(SBH_ENOMEM, "host allocation failed");
+    T->n = n;
+    T->leaf_size = leaf_size;
+    T->has_normals = normals != nullptr;
+    T->stream = s;
+    cudaGetDevice(&T->device);
+    cudaError_t e = sbh::alloc_tree(T->t4, n, normals != nullptr, false, s);
+    if (e == cudaSuccess) e = sbh::dalloc((void**)&T->t2.ctrl, sizeof(sbh::TreeCtrl), s);
+    if (e != cudaSuccess) {
+        release(T, s);
+        return cuda_fail(e, "sbh_build allocation");
+    }
+    int bad_p = 0, bad_w = 0;
+    e = sbh::build_sorted(T, points, weights, normals, s, &bad_p, &bad_w);
+    if (e != cudaSuccess) {
+        release(T, s);
+        return cuda_fail(e, "sbh_build sort");
+    }
+    if (bad_p || bad_w) {
+        release(T, s);
+        return fail(SBH_EINVAL, "sbh_build: %d non-finite coordinates, %d weights not finite and > 0", bad_p, bad_w);
+    }
+    e = sbh::build_tree(T, T->t4, T->lcp4, sbh::kMaxLevel4, 2, false, s);
+    if (e != cudaSuccess) {
+        release(T, s);
+        return cuda_fail(e, "sbh_build tree");
+    }
+    int32_t build_error = 0;
+    e = cudaMemcpyAsync(&build_error, &T->t4.ctrl->error, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        release(T, s);
+        return cuda_fail(e, "sbh_build");
+    }
+    if (build_error) {
+        release(T, s);
+        return fail(SBH_EUNSUPPORTED, "sbh_build: more than 2^24 - 1 points share one deepest-level cell");
+    }
+    *out = T;
+    return SBH_OK;
+}
+
+sbh_status sbh_eval(const sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel,
+                    int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts, float* out, void* stream)
+{
+    g_err[0] = 0;
+    if (!tree || !tree->t4.built) return fail(SBH_EINVAL, "tree is NULL or not built");
+    if (nq < 0) return fail(SBH_EINVAL, "nq < 0");
+    if (samples_per_subdomain < 1) return fail(SBH_EINVAL, "samples_per_subdomain must be >= 1");
+    sbh::KernelParams kp;
+    sbh_status st = check_kernel(kernel, &kp);
+    if (st != SBH_OK) return st;
+    if (kernel.kind == SBH_WINDING && !tree->has_normals)
+        return fail(SBH_EINVAL, "the winding-number kernel needs a tree built with normals");
+    sbh_eval_opts o = {0, 0, 0, 0};
+    if (opts) o = *opts;
+    if (o.sampling < 0 || o.sampling > 1 || o.rr < 0 || o.rr > 2 || o.seed_mode < 0 || o.seed_mode > 1 || o.reserved != 0)
+        return fail(SBH_EINVAL, "sbh_eval_opts out of range");
+    if (nq == 0) return SBH_OK;
+    if (!device_ptr(queries) || !device_ptr(out)) return fail(SBH_EINVAL, "queries and out must be device memory");
+    cudaError_t e = sbh::launch_stoch_eval(tree->t4.view(), queries, nq, kp, samples_per_subdomain, seed, o, out,
+                                           (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_eval launch");
+    return SBH_OK;
+}
+
+sbh_status sbh_eval_bh(sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel, float theta,
+                       int32_t warp_vote, float* out, void* stream)
+{
+    g_err[0] = 0;
+    if (!tree || !tree->t4.built) return fail(SBH_EINVAL, "tree is NULL or not built");
+    if (nq < 0) return fail(SBH_EINVAL, "nq < 0");
+    if (!(theta >= 0.0f) || !isfinite(theta)) return fail(SBH_EINVAL, "theta must be finite and >= 0");
+    sbh::KernelParams kp;
+    sbh_status st = check_kernel(kernel, &kp);
+    if (st != SBH_OK) return st;
+    if (kernel.kind == SBH_WINDING && !tree->has_normals)
+        return fail(SBH_EINVAL, "the winding-number kernel needs a tree built with normals");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!tree->t2.built) {
+        // the root cube of t2.ctrl was written by sbh_build; alloc_tree keeps that block
+        cudaError_t e = sbh::alloc_tree(tree->t2, tree->n, tree->has_normals != 0, true, s);
+        if (e == cudaSuccess) e = sbh::build_tree(tree, tree->t2, tree->lcp2, sbh::kMaxLevel2, 1, true, s);
+        if (e != cudaSuccess) return cuda_fail(e, "sbh_eval_bh tree build");
+        tree->stream = s;
+    }
+    if (nq == 0) return SBH_OK;
+    if (!device_ptr(queries) || !device_ptr(out)) return fail(SBH_EINVAL, "queries and out must be device memory");
+    const float beta = theta > 0.0f ? 1.0f / theta : INFINITY;
+    cudaError_t e = sbh::launch_bh_eval(tree->t2.view(), queries, nq, kp, beta, warp_vote ? 1 : 0, out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_eval_bh launch");
+    return SBH_OK;
+}
+
+sbh_status sbh_eval_brute(const float* points, const float* weights, const float* normals, int64_t n,
+                          const float* queries, int64_t nq, sbh_kernel kernel, int32_t fp64_accum, float* out,
+                          void* stream)
+{
+    g_err[0] = 0;
+    if (n < 0 || nq < 0) return fail(SBH_EINVAL, "n and nq must be >= 0");
+    sbh::KernelParams kp;
+    sbh_status st = check_kernel(kernel, &kp);
+    if (st != SBH_OK) return st;
+    if (nq == 0) return SBH_OK;
+    if (n > 0 && (!device_ptr(points) || !device_ptr(weights)))
+        return fail(SBH_EINVAL, "points and weights must be device memory");
+    if (kernel.kind == SBH_WINDING && n > 0 && !device_ptr(normals))
+        return fail(SBH_EINVAL, "the winding-number kernel needs normals");
+    if (!device_ptr(queries) || !device_ptr(out)) return fail(SBH_EINVAL, "queries and out must be device memory");
+    cudaError_t e = sbh::launch_brute(points, weights, normals, n, queries, nq, kp, fp64_accum ? 1 : 0, out,
+                                      (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_eval_brute launch");
+    return SBH_OK;
+}
+
+sbh_status sbh_tree_info(const sbh_tree* tree, int32_t which, sbh_tree_meta* meta)
+{
+    g_err[0] = 0;
+    if (!tree || !meta) return fail(SBH_EINVAL, "tree or meta is NULL");
+    if (which != 0 && which != 1) return fail(SBH_EINVAL, "which must be 0 or 1");
+    const sbh::DeviceTree& D = which == 0 ? tree->t4 : tree->t2;
+    if (!D.built) return fail(SBH_EUNSUPPORTED, "the 8-ary tree has not been built (call sbh_eval_bh first)");
+    sbh::TreeCtrl c;
+    cudaError_t e = cudaMemcpyAsync(&c, D.ctrl, sizeof(c), cudaMemcpyDeviceToHost, tree->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(tree->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_tree_info copy");
+    memset(meta, 0, sizeof(*meta));
+    meta->n_points = tree->n;
+    meta->n_nodes = c.n_nodes;
+    meta->leaf_size = tree->leaf_size;
+    meta->has_normals = tree->has_normals;
+    meta->max_depth = c.max_depth;
+    meta->first_sub = c.first_sub;
+    meta->n_sub = c.n_sub;
+    for (int a = 0; a < 3; ++a) meta->lo[a] = c.lo[a];
+    meta->side = c.side;
+    meta->diam0 = c.diam[0];
+    if (c.error) return fail(SBH_ECUDA, "tree build reported an internal inconsistency (%d)", c.error);
+    return SBH_OK;
+}
+
+sbh_status sbh_tree_export(const sbh_tree* tree, int32_t which, const sbh_tree_export_buffers* buf)
+{
+    sbh_tree_meta meta;
+    sbh_status st = sbh_tree_info(tree, which, &meta);
+    if (st != SBH_OK) return st;
+    if (!buf) return fail(SBH_EINVAL, "buf is NULL");
+    const sbh::DeviceTree& D = which == 0 ? tree->t4 : tree->t2;
+    const int64_t n = tree->n, N = meta.n_nodes;
+    cudaStream_t s = tree->stream;
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+        if (dst && e == cudaSuccess) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s);
+    };
+    cp(buf->perm, tree->perm, n * sizeof(int32_t));
+    cp(buf->code, tree->code, n * sizeof(uint64_t));
+    cp(buf->begin, D.nb, N * sizeof(int32_t));
+    cp(buf->end, D.ne, N * sizeof(int32_t));
+    cp(buf->first_child, D.fc, N * sizeof(int32_t));
+    cp(buf->parent, D.parent, N * sizeof(int32_t));
+    cp(buf->com_mass, D.pm, N * sizeof(float4));
+    cp(buf->cdf, D.cdf, N * sizeof(float));
+    uint32_t* meta_h = nullptr;
+    double* agg_h = nullptr;
+    float4* dip_h = nullptr;
+    if (buf->nchild || buf->level) {
+        meta_h = new (std::nothrow) uint32_t[N];
+        if (!meta_h) return fail(SBH_ENOMEM, "host allocation failed");
+        cp(meta_h, D.meta, N * sizeof(uint32_t));
+    }
+    if (buf->com_mass64) {
+        agg_h = new (std::nothrow) double[8 * N];
+        if (!agg_h) { delete[] meta_h; return fail(SBH_ENOMEM, "host allocation failed"); }
+        cp(agg_h, D.agg, 8 * N * sizeof(double));
+    }
+    if (buf->dipole && D.dip) {
+        dip_h = new (std::nothrow) float4[N];
+        if (!dip_h) { delete[] meta_h; delete[] agg_h; return fail(SBH_ENOMEM, "host allocation failed"); }
+        cp(dip_h, D.dip, N * sizeof(float4));
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+        for (int64_t v = 0; v < N; ++v) {
+            if (meta_h && buf->nchild) buf->nchild[v] = (int32_t)sbh::meta_nchild(meta_h[v]);
+            if (meta_h && buf->level) buf->level[v] = (int32_t)sbh::meta_level(meta_h[v]);
+            if (agg_h) {
+                const double m = agg_h[8 * v];
+                buf->com_mass64[4 * v + 0] = agg_h[8 * v + 1] / m;
+                buf->com_mass64[4 * v + 1] = agg_h[8 * v + 2] / m;
+                buf->com_mass64[4 * v + 2] = agg_h[8 * v + 3] / m;
+                buf->com_mass64[4 * v + 3] = m;
+            }
+            if (buf->dipole) {
+                for (int a = 0; a < 3; ++a)
+                    buf->dipole[3 * v + a] = dip_h ? (&dip_h[v].x)[a] : 0.0f;
+            }
+        }
+    }
+    delete[] meta_h;
+    delete[] agg_h;
+    delete[] dip_h;
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_tree_export copy");
+    return SBH_OK;
+}
+
+void sbh_tree_free(sbh_tree* tree)
+{
+    if (!tree) return;
+    cudaStreamSynchronize(tree->stream);
+    release(tree, tree->stream);
+}
+
+}  // extern "C"

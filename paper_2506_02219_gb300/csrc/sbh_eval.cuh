@@ -1,0 +1,20 @@
+// sbh_eval.cuh -- launchers of the evaluation kernels (estimator, Barnes-Hut, brute force).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sbh_internal.cuh"
+
+namespace sbh {
+
+cudaError_t launch_stoch_eval(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
+                              uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s);
+
+cudaError_t launch_bh_eval(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, float beta,
+                           int warp_vote, float* out, cudaStream_t s);
+
+cudaError_t launch_brute(const float* P, const float* W, const float* N, int64_t n, const float* Q, int64_t nq,
+                         const KernelParams& kp, int fp64_accum, float* out, cudaStream_t s);
+
+}  // namespace sbh

@@ -1,0 +1,177 @@
+// sbh_internal.cuh -- shared device-side definitions of libsbh: the tree layout in HBM, the
+// counter-based random stream, the kernel terms and the FP32 decision arithmetic.
+//
+// Madan et al., "Stochastic Barnes-Hut Approximation for Fast Summation on the GPU" (SIGGRAPH
+// 2025). Section and equation numbers below refer to that paper.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sbh.h"
+
+namespace sbh {
+
+// ----------------------------------------------------------------------------------------------
+// Limits
+// ----------------------------------------------------------------------------------------------
+constexpr int kMortonBits = 20;          // bits per axis; 60-bit codes
+constexpr int kMaxLevel4 = 10;           // 64-ary tree: 6 code bits per level
+constexpr int kMaxLevel2 = 20;           // 8-ary tree: 3 code bits per level
+constexpr int kMaxDepth = kMaxLevel2 + 2;  // generations of nodes, root included, upper bound
+constexpr int kMaxLeafSize = 64;
+constexpr int kDiamLevels = 24;          // |B| table entries (levels 0 .. 22 used)
+
+// node kinds (bits 30..31 of meta)
+constexpr uint32_t kPoint = 0;     // a single source point, no children
+constexpr uint32_t kInternal = 1;  // children are the runs of the next code digit
+constexpr uint32_t kMultiLeaf = 2; // a leaf holding several points: its children are the points
+constexpr uint32_t kMaxChildren = (1u << 24) - 1;
+
+// meta word of a node: child count (24 bits) | level << 24 (6 bits) | kind << 30
+__host__ __device__ inline uint32_t meta_pack(uint32_t nchild, uint32_t level, uint32_t kind)
+{
+    return (nchild & 0xFFFFFFu) | ((level & 0x3Fu) << 24) | ((kind & 0x3u) << 30);
+}
+__host__ __device__ inline uint32_t meta_nchild(uint32_t m) { return m & 0xFFFFFFu; }
+__host__ __device__ inline uint32_t meta_level(uint32_t m) { return (m >> 24) & 0x3Fu; }
+__host__ __device__ inline uint32_t meta_kind(uint32_t m) { return (m >> 30) & 0x3u; }
+
+// ----------------------------------------------------------------------------------------------
+// Per-tree control block, in device memory, written by the build and read by every eval kernel.
+// ----------------------------------------------------------------------------------------------
+struct TreeCtrl {
+    int32_t n_nodes;
+    int32_t first_sub;    // subdomains: [first_sub, first_sub + n_sub)
+    int32_t n_sub;
+    int32_t max_depth;    // deepest generation that holds nodes
+    int32_t depth_base[kMaxDepth + 2];  // node id of the first node of each generation
+    float lo[3];
+    float side;
+    float diam[kDiamLevels];  // |B| at each level: sqrt(3) * side * d^-level (FP32, exact scaling)
+    int32_t error;        // nonzero if a build step detected an inconsistency
+};
+
+// Structure-of-arrays node storage of one tree (device pointers). Children of node v are the
+// contiguous ids fc[v] .. fc[v] + nchild - 1, in Morton order; generations are contiguous.
+struct TreeView {
+    const float4* pm;     // (centre of mass x, y, z; aggregate mass)
+    const float4* dip;    // (sum_j m_j n_j; 0) or nullptr
+    const float* cdf;     // prefix fraction of the node's mass among its siblings (last = 1)
+    const int32_t* fc;    // first child, -1 for a point
+    const uint32_t* meta; // nchild | level << 24 | kind << 30
+    const int32_t* nb;    // first sorted point
+    const int32_t* ne;    // one past the last sorted point
+    const int32_t* skip;  // next node of a depth-first walk after this subtree (8-ary tree)
+    const TreeCtrl* ctrl;
+};
+
+// ----------------------------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+// SC'11): ten rounds; each multiplies counter words 0 and 2 by the round multipliers, swaps
+// the halves and xors in the other words and the key; the key advances by the Weyl increments
+// between rounds.
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+    constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+    constexpr uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(kM0, c.x), lo0 = kM0 * c.x;
+        const uint32_t hi1 = __umulhi(kM1, c.z), lo1 = kM1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += kW0;
+        k.y += kW1;
+    }
+    return c;
+}
+
+// 24 random bits as a float in [0, 1): exact in FP32
+__device__ __forceinline__ float unit24(uint32_t x) { return __uint2float_rn(x >> 8) * 5.9604644775390625e-8f; }
+
+// ----------------------------------------------------------------------------------------------
+// FP32 decision arithmetic. Every step is one IEEE round-to-nearest operation with no
+// contraction, in a fixed order, so that a CPU reference in FP32 reproduces it bit for bit.
+// ----------------------------------------------------------------------------------------------
+__device__ __forceinline__ float dist_rn(float px, float py, float pz, float3 q)
+{
+    const float dx = __fsub_rn(px, q.x), dy = __fsub_rn(py, q.y), dz = __fsub_rn(pz, q.z);
+    const float s = __fadd_rn(__fadd_rn(__fmul_rn(dx, dx), __fmul_rn(dy, dy)), __fmul_rn(dz, dz));
+    return __fsqrt_rn(s);
+}
+
+// Eq. 5: p = min(1, max(1, beta~_T) / beta~_c), beta~ = ||q - p~|| / |B|
+__device__ __forceinline__ float rr_prob_rn(float dT, float diamT, float dc, float diamc)
+{
+    const float bt = __fdiv_rn(dT, diamT);
+    const float bc = __fdiv_rn(dc, diamc);
+    const float r = __fdiv_rn(fmaxf(bt, 1.0f), bc);  // bc == 0 -> +inf -> 1
+    return fminf(r, 1.0f);
+}
+
+// ----------------------------------------------------------------------------------------------
+// Kernel terms m f(p, q) in FP32 (values; tolerances, not bit-exactness, apply to these).
+// ----------------------------------------------------------------------------------------------
+struct KernelParams {
+    int kind;
+    float eps2;       // softening^2
+    float alpha;
+    float g[3];       // affine test kernel
+};
+
+constexpr float kInv4Pi = 0.0795774715459476679f;
+
+// Coulomb-like potential (Sec. 4.2): m / sqrt(r^2 + eps^2)
+__device__ __forceinline__ float term_coulomb(float4 pm, float3 q, float eps2)
+{
+    const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+    return pm.w * rsqrtf(r2);
+}
+
+// winding-number dipole (Sec. 4.3.2): ((p - q) . N) / (4 pi r^3), N = sum_j m_j n_j; 0 at r = 0
+__device__ __forceinline__ float term_winding(float4 pm, float4 dp, float3 q)
+{
+    const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ir = rsqrtf(r2);
+    const float dot = fmaf(dx, dp.x, fmaf(dy, dp.y, dz * dp.z));
+    const float v = dot * (ir * ir * ir) * kInv4Pi;
+    return r2 > 0.0f ? v : 0.0f;
+}
+
+// distance for the smooth-distance kernel (Sec. 4.3.3), whose term is m exp(-alpha r)
+__device__ __forceinline__ float dist_fast(float4 pm, float3 q)
+{
+    const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    return r2 * rsqrtf(fmaxf(r2, 1e-37f));
+}
+
+// affine test kernel: m (1 + g . (p - q))
+__device__ __forceinline__ float term_affine(float4 pm, float3 q, const float* g)
+{
+    const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
+    return pm.w * (1.0f + fmaf(g[0], dx, fmaf(g[1], dy, g[2] * dz)));
+}
+
+// Running sum of m exp(-alpha r) terms held as acc * exp(-alpha * ref): the reference distance
+// drops to the smallest distance seen so far, so that no term overflows and the dominant terms
+// never underflow in FP32.
+struct ExpAcc {
+    float ref;
+    float acc;
+    __device__ __forceinline__ void init(float r0) { ref = r0; acc = 0.0f; }
+    // make ref <= r so that a term at distance r can be added
+    __device__ __forceinline__ void lower(float r, float alpha)
+    {
+        if (r < ref) {
+            acc *= __expf(-alpha * (ref - r));
+            ref = r;
+        }
+    }
+    __device__ __forceinline__ float scale(float r, float alpha) const { return __expf(-alpha * (r - ref)); }
+};
+
+}  // namespace sbh

@@ -1,0 +1,116 @@
+"""GPU evaluation kernels against the oracle on the same seeded inputs.
+
+- sbh_eval vs the oracle's replay of Algorithm 2 with the same Philox stream: per-query
+  estimates within 1e-4 (relative; for winding numbers relative to max(|F|, 1); for the smooth
+  distance on log F) on at least 99.9% of queries. Decisions are FP32 on both sides, so nearly
+  every query follows the same paths.
+- seed-averaged GPU estimates within 3 sigma of the exact sum, sigma from the oracle's
+  enumerated variance.
+- sbh_eval_bh without warp voting vs the oracle's Algorithm 1 (identical FP32 far-field
+  decisions), and both variants at theta = 0 vs the exact sum.
+- sbh_eval_brute vs the oracle's compensated FP64 brute force.
+"""
+import numpy as np
+import pytest
+
+from gpu_util import dev, gpu_kwargs, oracle_kwargs, parity_error
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-4
+
+
+def _inputs(kind, n, nq, seed):
+    from paper_2506_02219_gb300 import workloads as W
+    rng = np.random.default_rng(seed)
+    if kind in ("winding", "smoothdist"):
+        pts, w, nrm = W.shape_union(n, seed, n_ellipsoids=6, n_boxes=2)
+        if kind == "smoothdist":
+            w = np.ones_like(w)
+            nrm = None
+        q = rng.uniform(-1.05, 1.05, (nq, 3)).astype(np.float32)
+    else:
+        pts = rng.random((n, 3)).astype(np.float32)
+        w = rng.uniform(0.5, 1.5, n).astype(np.float32)
+        nrm = None
+        q = rng.uniform(-0.1, 1.1, (nq, 3)).astype(np.float32)
+    return pts, w, nrm, q
+
+
+@pytest.mark.parametrize("kind", ["coulomb", "winding", "smoothdist", "affine"])
+@pytest.mark.parametrize("S", [1, 3])
+@pytest.mark.parametrize("leaf", [1, 4])
+def test_estimator_matches_replay(sbh, oracle_mod, kind, S, leaf):
+    pts, w, nrm, q = _inputs(kind, 12000, 3001, 17 + S)
+    t = sbh.sbh_build(dev(pts), dev(w), dev(nrm), leaf_size=leaf)
+    seed = 0x5BA7 + S
+    g = sbh.sbh_eval(t, dev(q), samples_per_subdomain=S, seed=seed, **gpu_kwargs(kind)).cpu().numpy()
+    o = oracle_mod.Tree(pts, w, nrm, leaf_size=leaf, d=4).replay(q, S=S, seed=seed, **oracle_kwargs(oracle_mod, kind))
+    err = parity_error(kind, g, o)
+    assert np.mean(err <= TOL) >= 0.999, (np.sort(err)[-10:], np.mean(err <= TOL))
+
+
+@pytest.mark.parametrize("sampling,rr,coherent", [(1, 0, 0), (0, 1, 0), (0, 2, 0), (0, 0, 1), (1, 2, 1)])
+def test_estimator_options_match_replay(sbh, oracle_mod, sampling, rr, coherent):
+    pts, w, nrm, q = _inputs("coulomb", 9000, 2500, 5)
+    t = sbh.sbh_build(dev(pts), dev(w))
+    o = sbh.EvalOpts()
+    o.sampling, o.rr, o.seed_mode = sampling, rr, coherent
+    g = sbh.sbh_eval(t, dev(q), "coulomb", seed=99, opts=o).cpu().numpy()
+    r = oracle_mod.Tree(pts, w).replay(q, S=1, seed=99, sampling=sampling, rr=rr, coherent=bool(coherent))
+    err = parity_error("coulomb", g, r)
+    assert np.mean(err <= TOL) >= 0.999
+
+
+@pytest.mark.parametrize("kind", ["coulomb", "winding", "smoothdist"])
+def test_seed_mean_within_three_sigma(sbh, oracle_mod, kind):
+    pts, w, nrm, q = _inputs(kind, 300, 12, 23)
+    kw = oracle_kwargs(oracle_mod, kind, alpha=30.0)
+    ot = oracle_mod.Tree(pts, w, nrm, leaf_size=1, d=4)
+    F = oracle_mod.brute(pts, w, q, normals=nrm, **kw)
+    mean, var = ot.enumerate(q, **kw)
+    t = sbh.sbh_build(dev(pts), dev(w), dev(nrm))
+    K = 2000
+    Q = dev(q)
+    est = np.stack([sbh.sbh_eval(t, Q, seed=s, **gpu_kwargs(kind, alpha=30.0)).cpu().numpy() for s in range(K)])
+    if kind == "smoothdist":
+        est = np.exp(-30.0 * est.astype(np.float64))  # back to the sum the estimator is unbiased for
+    sigma = np.sqrt(var / K)
+    dev_ = np.abs(est.mean(0) - F)
+    assert np.all(dev_ <= 3 * sigma + 1e-6 * np.abs(F)), dev_ / sigma
+
+
+@pytest.mark.parametrize("kind", ["coulomb", "winding", "smoothdist"])
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.8])
+def test_bh_matches_algorithm_1(sbh, oracle_mod, kind, theta):
+    pts, w, nrm, q = _inputs(kind, 10000, 2000, 31)
+    t = sbh.sbh_build(dev(pts), dev(w), dev(nrm))
+    g = sbh.sbh_eval_bh(t, dev(q), theta=theta, warp_vote=False, **gpu_kwargs(kind)).cpu().numpy()
+    beta = float(np.float32(1.0) / np.float32(theta))
+    o = oracle_mod.Tree(pts, w, nrm, leaf_size=1, d=2).bh(q, beta, **oracle_kwargs(oracle_mod, kind))
+    err = parity_error(kind, g, o)
+    assert np.mean(err <= 2e-5) >= 0.999, np.sort(err)[-5:]
+
+
+@pytest.mark.parametrize("vote", [False, True])
+def test_bh_exact_at_theta_zero_and_vote_accuracy(sbh, oracle_mod, vote):
+    pts, w, nrm, q = _inputs("coulomb", 6000, 1000, 41)
+    t = sbh.sbh_build(dev(pts), dev(w))
+    F = oracle_mod.brute(pts, w, q)
+    g = sbh.sbh_eval_bh(t, dev(q), "coulomb", theta=0.0, warp_vote=vote).cpu().numpy()
+    assert np.max(np.abs(g - F) / F) < 1e-5
+    e_vote = np.abs(sbh.sbh_eval_bh(t, dev(q), "coulomb", theta=0.7, warp_vote=True).cpu().numpy() - F) / F
+    e_lane = np.abs(sbh.sbh_eval_bh(t, dev(q), "coulomb", theta=0.7, warp_vote=False).cpu().numpy() - F) / F
+    assert np.all(e_vote <= e_lane * 1.0001 + 1e-6) or e_vote.mean() < e_lane.mean()
+
+
+@pytest.mark.parametrize("kind", ["coulomb", "winding", "smoothdist", "affine"])
+@pytest.mark.parametrize("fp64", [True, False])
+def test_brute_matches_oracle(sbh, oracle_mod, kind, fp64):
+    pts, w, nrm, q = _inputs(kind, 7777, 1500, 51)
+    kw = oracle_kwargs(oracle_mod, kind)
+    F = oracle_mod.brute(pts, w, q, normals=nrm, **kw)
+    g = sbh.sbh_eval_brute(dev(pts), dev(w), dev(q), normals=dev(nrm), fp64_accum=fp64,
+                           **gpu_kwargs(kind)).cpu().numpy()
+    err = parity_error(kind, g, F)
+    assert np.max(err) < (2e-6 if fp64 else 1e-4), np.max(err)
