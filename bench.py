@@ -1,0 +1,500 @@
+#!/usr/bin/env python3
+"""Benchmark of the stochastic Barnes-Hut hot path on one or more GB300s.
+
+A step is one pass of the whole hot path over one batch: the GPU tree build (bounds, Morton
+codes, radix sort, topology, aggregates) followed by the stratified path estimator at every query.
+The default workload is the winding-number problem: 2^20 oriented, area-weighted surface samples on
+a union of 8 random ellipsoids, evaluated on the 256^3 cell-centred grid of their bounding box,
+S = 1 path per subdomain, leaf size 1.
+
+Printed (rank 0, one JSON line): whole-job queries/s over the timed steps, the end-to-end number
+through the public API with pinned host buffers, the roofline of the estimator kernel, the CPU
+oracle's throughput, clocks sampled during the timed region, and the equal-median-error comparison
+with the project's own GPU Barnes-Hut (theta sweep, log-log interpolation).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+With N > 1 it runs under torchrun, one replica per GPU (each rank its own seeded problem), no
+collective on the data path; the timed region is bracketed by barriers and the time is the maximum
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "queries/sec at equal median rel. error vs own GPU deterministic BH; % roofline"
+L2_BYTES = 129 * 1024 * 1024
+
+# FP32 floating-point operations of one kernel term as written in the CUDA kernels (an FMA counts
+# 2, a multiply, add, rsqrt or exp 1): Coulomb 3 sub + r^2 with eps^2 (3 FMA) + rsqrt + scale +
+# accumulate; winding 3 sub + r^2 (2 FMA + mul) + rsqrt + r^-3 (2 mul) + (p - q).N (2 FMA + mul) +
+# 2 mul + accumulate; smooth distance 3 sub + r^2 (2 FMA + mul) + r (rsqrt, mul) + compare +
+# alpha (d - ref) (sub, mul) + exp + FMA; affine 3 sub + g.(p - q) (2 FMA + mul) + add + mul + add.
+FLOPS_PER_TERM = {"coulomb": 12, "winding": 19, "smoothdist": 16, "affine": 11}
+# FP32 lanes per SM and SMs of a GB300: 128 x 152, two flops per lane per cycle (FMA)
+FP32_LANES = 152 * 128
+
+
+def workload_by_name(name: str, rank: int = 0):
+    from paper_2506_02219_gb300 import workloads as W
+    b = W.BASE_SEED
+    if name == "winding":
+        return W.winding_ellipsoids(seed=b + 1 + 1000 * rank)
+    if name == "cube":
+        return W.coulomb_cube(seed=b + 0 + 1000 * rank)
+    if name == "slice_coulomb":
+        return W.slice_plane_shapes(kernel="coulomb", seed=b + 2 + 1000 * rank)
+    if name == "slice_smoothdist":
+        return W.slice_plane_shapes(kernel="smoothdist", seed=b + 2 + 1000 * rank)
+    raise ValueError(name)
+
+
+# ------------------------------------------------------------------------------------------------
+# distributed plumbing (also exercised on CPU with gloo by the tests)
+# ------------------------------------------------------------------------------------------------
+def dist_env():
+    """(rank, world_size, local_rank) from the torchrun environment (defaults: single process)."""
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def weak_scaling_value(units_per_rank: float, world: int, max_seconds: float) -> float:
+    """Whole-job throughput: every rank processed units_per_rank in at most max_seconds."""
+    return units_per_rank * world / max_seconds
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        mhz, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower() == "active":
+                    reasons.add(name)
+        if not mhz:
+            return None
+        return {"sm_mhz": float(np.median(mhz)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ------------------------------------------------------------------------------------------------
+# helpers
+# ------------------------------------------------------------------------------------------------
+def _kernel_kwargs(wl):
+    return dict(kernel=wl.kernel, softening=wl.softening, alpha=wl.alpha)
+
+
+def rel_error(kind, est, ref):
+    """Per-query relative error: |F^ - F| / |F|; winding numbers / max(|F|, 1); smooth distance on
+    the distance, / max(|d|, h) with h = 2/1000 the spacing of the 1000^2 slice plane."""
+    est = np.asarray(est, np.float64)
+    ref = np.asarray(ref, np.float64)
+    if kind == "winding":
+        return np.abs(est - ref) / np.maximum(np.abs(ref), 1.0)
+    if kind == "smoothdist":
+        return np.abs(est - ref) / np.maximum(np.abs(ref), 2.0 / 1000.0)
+    return np.abs(est - ref) / np.abs(ref)
+
+
+def interp_loglog(x_target, xs, ys):
+    """Linear interpolation of log(y) against log(x) at x_target (as in the paper's Fig. 4);
+    returns (y, extrapolated)."""
+    xs = np.asarray(xs, np.float64)
+    ys = np.asarray(ys, np.float64)
+    order = np.argsort(xs)
+    lx, ly = np.log(xs[order]), np.log(ys[order])
+    t = np.log(x_target)
+    if t < lx[0] or t > lx[-1]:
+        i = 0 if t < lx[0] else len(lx) - 2
+        slope = (ly[i + 1] - ly[i]) / (lx[i + 1] - lx[i]) if lx[i + 1] != lx[i] else 0.0
+        return float(np.exp(ly[i] + slope * (t - lx[i]))), True
+    return float(np.exp(np.interp(t, lx, ly))), False
+
+
+def source_hash(paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+EVAL_SOURCES = ["paper_2506_02219_gb300/csrc/sbh_eval.cu", "paper_2506_02219_gb300/csrc/sbh_internal.cuh"]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per query of the estimator kernel from the committed ncu summary, if the kernel
+    sources still hash to what was profiled; else None."""
+    path = os.path.join(ROOT, "profiles", f"sbh_stoch_eval_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    want = source_hash(EVAL_SOURCES)
+    vals = {}
+    for ln in open(path):
+        if ln.startswith("<!-- ") and "=" in ln:
+            k, v = ln[5:].strip().rstrip("->").strip().split("=", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != want or "dram_bytes_per_query" not in vals:
+        return None
+    return float(vals["dram_bytes_per_query"])
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle timing (the cpu_baseline leg and the reference arm)
+# ------------------------------------------------------------------------------------------------
+def oracle_throughput(wl, seconds: float, S: int = 1):
+    """Time the oracle on the host cores: its tree build over all sources plus its replay of a
+    sample of queries sized to about `seconds` of work; returns (queries/s extrapolated to the full
+    query set, cores used, description of the sample)."""
+    import oracle
+    kinds = {"coulomb": oracle.COULOMB, "winding": oracle.WINDING, "smoothdist": oracle.SMOOTHDIST}
+    cores = oracle.max_threads()
+    t0 = time.perf_counter()
+    tree = oracle.Tree(wl.points, wl.weights, wl.normals, leaf_size=wl.leaf_size, d=4)
+    t_build = time.perf_counter() - t0
+    nq = wl.queries.shape[0]
+    rng = np.random.default_rng(5)
+    pilot = min(nq, 8192)
+    idx = rng.choice(nq, pilot, replace=False)
+    t0 = time.perf_counter()
+    tree.replay(wl.queries[idx], S=S, seed=7, kind=kinds[wl.kernel], softening=wl.softening, alpha=wl.alpha,
+                query_index=idx)
+    per_q = (time.perf_counter() - t0) / pilot
+    n_sample = int(min(nq, max(pilot, (seconds - t_build) / max(per_q, 1e-9))))
+    idx = rng.choice(nq, n_sample, replace=False)
+    t0 = time.perf_counter()
+    tree.replay(wl.queries[idx], S=S, seed=7, kind=kinds[wl.kernel], softening=wl.softening, alpha=wl.alpha,
+                query_index=idx)
+    t_replay = time.perf_counter() - t0
+    t_full = t_build + t_replay * nq / n_sample
+    desc = (f"oracle tree build over all {wl.points.shape[0]} sources ({t_build:.2f} s) + replay of "
+            f"{n_sample} random queries of {nq} ({t_replay:.2f} s), replay time scaled linearly to all queries")
+    return nq / t_full, cores, desc, t_full
+
+
+# ------------------------------------------------------------------------------------------------
+# the GPU arm
+# ------------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    import paper_2506_02219_gb300 as sbh
+    from paper_2506_02219_gb300 import _build
+    _build.build()
+    sbh.load_library()
+
+    wl = workload_by_name(args.workload, rank)
+    S, seed = args.S, 0x5BA7 + rank
+    n, nq = wl.points.shape[0], wl.queries.shape[0]
+    P = torch.from_numpy(wl.points).to(dev)
+    M = torch.from_numpy(wl.weights).to(dev)
+    N = torch.from_numpy(wl.normals).to(dev) if (wl.normals is not None and wl.kernel == "winding") else None
+    Q = torch.from_numpy(wl.queries).to(dev)
+    out = torch.empty(nq, dtype=torch.float32, device=dev)
+    kk = _kernel_kwargs(wl)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(keep):
+        tree = sbh.sbh_build(P, M, N, leaf_size=wl.leaf_size)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sbh.sbh_eval(tree, Q, samples_per_subdomain=S, seed=seed, out=out, **kk)
+        e1.record(stream)
+        keep.append(tree)
+        return e0, e1
+
+    keep = []
+    for _ in range(args.warmup):
+        step(keep)
+    torch.cuda.synchronize()
+    for t in keep:
+        t.free()
+    keep = []
+    input_bytes = Q.numel() * 4 + P.numel() * 4 + M.numel() * 4 + (N.numel() * 4 if N is not None else 0)
+
+    clocks = ClockSampler(local if world > 1 else 0)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = sbh.sbh_kernel_launches()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    evs = [step(keep) for _ in range(args.steps)]
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = sbh.sbh_kernel_launches() - launches0
+    clk = clocks.stop()
+    step_ms = t0.elapsed_time(t1) / args.steps
+    eval_ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    for t in keep:
+        t.free()
+    max_s = reduce_max(step_ms * args.steps / 1e3, world, dev)
+    value = weak_scaling_value(nq * args.steps, world, max_s)
+
+    # end to end through the public API with pinned host buffers
+    Ph = torch.from_numpy(wl.points).pin_memory()
+    Mh = torch.from_numpy(wl.weights).pin_memory()
+    Nh = torch.from_numpy(wl.normals).pin_memory() if N is not None else None
+    Qh = torch.from_numpy(wl.queries).pin_memory()
+    Oh = torch.empty(nq, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        Pd = Ph.to(dev, non_blocking=True)
+        Md = Mh.to(dev, non_blocking=True)
+        Nd = Nh.to(dev, non_blocking=True) if Nh is not None else None
+        Qd = Qh.to(dev, non_blocking=True)
+        tree = sbh.sbh_build(Pd, Md, Nd, leaf_size=wl.leaf_size)
+        o = sbh.sbh_eval(tree, Qd, samples_per_subdomain=S, seed=seed, **kk)
+        Oh.copy_(o, non_blocking=True)
+        torch.cuda.synchronize()
+        tree.free()
+
+    for _ in range(2):
+        e2e_step()
+    barrier(world)
+    ts = time.perf_counter()
+    k_e2e = max(3, args.steps // 2)
+    for _ in range(k_e2e):
+        e2e_step()
+    e2e_s = reduce_max((time.perf_counter() - ts), world, dev)
+    h2d = Ph.numel() * 4 + Mh.numel() * 4 + (Nh.numel() * 4 if Nh is not None else 0) + Qh.numel() * 4
+    e2e = {"value": weak_scaling_value(nq * k_e2e, world, e2e_s), "unit": "queries/s",
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(nq * 4)}
+
+    result = {"metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+              "warmup": args.warmup, "ms_per_step": max_s * 1e3 / args.steps, "higher_is_better": True,
+              "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+              "config": {"workload": wl.name, "sources": int(n), "queries": int(nq), "kernel": wl.kernel,
+                         "samples_per_subdomain": S, "leaf_size": wl.leaf_size, "step": "sbh_build + sbh_eval",
+                         "l2": f"inputs larger than L2: {input_bytes / 2**20:.0f} MiB read per step, L2 129 MiB",
+                         "parallelism": f"replicas x{world}"},
+              "e2e": e2e, "gpu_launches": int(launches), "gpu_launches_per_step": launches / args.steps,
+              "clocks": clk, "eval_ms_per_step": eval_ms, "build_ms_per_step": step_ms - eval_ms}
+
+    if rank == 0:
+        # work of one estimator launch, counted by the same traversal
+        tree = sbh.sbh_build(P, M, N, leaf_size=wl.leaf_size)
+        cnt = sbh.sbh_eval_count(tree, Q, samples_per_subdomain=S, seed=seed, **kk)
+        c = np.array([cnt["terms"], cnt["records"], cnt["decisions"], cnt["cdf_reads"]], np.float64)
+        flops = c[0] * FLOPS_PER_TERM[wl.kernel]
+        sm_mhz = 2070.0
+        peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+        achieved = flops / (eval_ms / 1e3) / 1e12
+        traffic_pq = profiled_traffic(args.workload)
+        result["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                              "frac": achieved / peak,
+                              "traffic": (traffic_pq * nq) if traffic_pq is not None else None,
+                              "kernel": "k_stoch_eval", "terms_per_query": c[0] / nq,
+                              "records_per_query": c[1] / nq, "decisions_per_query": c[2] / nq,
+                              "flops_per_term": FLOPS_PER_TERM[wl.kernel],
+                              "peak_basis": "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
+        if not args.no_equal_error:
+            result["equal_error"] = equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev)
+        tree.free()
+        if world == 1 and not args.no_cpu_baseline:
+            v, cores, desc, _ = oracle_throughput(wl, args.cpu_seconds, S)
+            result["cpu_baseline"] = {"value": v, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                                      "sample": desc}
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
+    """Median relative error of the estimator (S = 1) against the exact sum, and the Barnes-Hut
+    theta sweep (time per query set, median error); the Barnes-Hut time at the estimator's median
+    error by log-log interpolation, as in the paper's Fig. 4."""
+    import torch
+    nq = Q.shape[0]
+    kk = _kernel_kwargs(wl)
+    g = torch.Generator(device="cpu").manual_seed(11)
+    idx = torch.randperm(nq, generator=g)[: min(nq, 65536)].sort().values.to(dev)
+    Qs = Q[idx].contiguous()
+    ref = sbh.sbh_eval_brute(P, M, Qs, normals=N, fp64_accum=True, **kk).cpu().numpy()
+    out = sbh.sbh_eval(tree, Q, samples_per_subdomain=S, seed=seed, **kk)
+    err_s = float(np.median(rel_error(wl.kernel, out[idx].cpu().numpy(), ref)))
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    extra = {}
+    for s2 in (2, 4):
+        o2 = sbh.sbh_eval(tree, Q, samples_per_subdomain=s2, seed=seed, **kk)
+        extra[f"S{s2}"] = {"ms": timed(lambda: sbh.sbh_eval(tree, Q, samples_per_subdomain=s2, seed=seed, out=o2, **kk), 2),
+                           "median_rel_err": float(np.median(rel_error(wl.kernel, o2[idx].cpu().numpy(), ref)))}
+    bh_out = torch.empty(nq, dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    sbh.sbh_eval_bh(tree, Q[:1], theta=0.5, **kk)  # builds the 8-ary tree
+    torch.cuda.synchronize()
+    bh_build_ms = (time.perf_counter() - t0) * 1e3
+    sweep = []
+    for vote in (True, False):
+        for theta in (3.0, 2.0, 1.5, 1.2, 1.0, 0.8, 0.67, 0.5, 0.4, 0.3, 0.25):
+            ms = timed(lambda: sbh.sbh_eval_bh(tree, Q, theta=theta, warp_vote=vote, out=bh_out, **kk))
+            e = sbh.sbh_eval_bh(tree, Qs, theta=theta, warp_vote=vote, **kk).cpu().numpy()
+            sweep.append({"theta": theta, "warp_vote": vote, "ms": ms,
+                          "median_rel_err": float(np.median(rel_error(wl.kernel, e, ref)))})
+    best = None
+    for vote in (True, False):
+        pts = [(s["median_rel_err"], s["ms"]) for s in sweep if s["warp_vote"] == vote and s["median_rel_err"] > 0]
+        t_bh, extrap = interp_loglog(err_s, [p[0] for p in pts], [p[1] for p in pts])
+        if best is None or t_bh < best[0]:
+            best = (t_bh, extrap, vote)
+    return {"stochastic": {"S": S, "ms": eval_ms, "median_rel_err": err_s, **extra},
+            "bh_sweep": sweep, "bh_tree_build_ms": bh_build_ms,
+            "bh_ms_at_equal_error": best[0], "bh_warp_vote": best[2], "extrapolated": best[1],
+            "speedup_vs_bh_at_equal_median_error": best[0] / eval_ms,
+            "error_reference": "GPU brute force with FP64 tile accumulation on 65536 random queries",
+            "time_basis": "evaluation kernels only, trees prebuilt (the paper excludes building)"}
+
+
+# ------------------------------------------------------------------------------------------------
+# the reference arm: the CPU oracle as it stands
+# ------------------------------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    wl = workload_by_name(args.workload, 0)
+    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_throughput(wl, per_step, args.S)
+    vals, ts = [], []
+    for _ in range(args.steps):
+        v, cores, desc, t_full = oracle_throughput(wl, per_step, args.S)
+        vals.append(v)
+        ts.append(t_full)
+    value = float(np.mean(vals))
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
+                      "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": float(np.mean(ts)) * 1e3, "higher_is_better": True, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": wl.name, "sources": int(wl.points.shape[0]),
+                                 "queries": int(wl.queries.shape[0]), "kernel": wl.kernel,
+                                 "samples_per_subdomain": args.S, "leaf_size": wl.leaf_size,
+                                 "step": "oracle tree build + Algorithm 2 replay (FP64, CPU)"},
+                      "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
+                                       "sample": desc},
+                      "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                              "d2h_bytes_per_step": 0}}), flush=True)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="winding", choices=["winding", "cube", "slice_coulomb", "slice_smoothdist"])
+    ap.add_argument("--S", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-equal-error", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

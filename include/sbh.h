@@ -72,7 +72,9 @@ typedef struct {
     int32_t rr;         /* 0: Eq. 5; 1: no Russian roulette (p = 1); 2: fixed p = 1/2 */
     int32_t seed_mode;  /* 0: random stream keyed by query index; 1: every query uses index 0
                            (coherent across queries, the paper's identical per-warp seeding) */
-    int32_t reserved;   /* must be 0 */
+    int32_t raw_sum;    /* SBH_SMOOTHDIST only: 1 returns the signed estimate of
+                           sum_i m_i exp(-alpha |p_i - q|) itself (FP32; underflows to 0 beyond
+                           alpha |p - q| ~ 87) instead of the distance -log(F) / alpha */
 } sbh_eval_opts;
 
 typedef struct sbh_tree sbh_tree;  /* opaque, library-owned */
@@ -138,6 +140,16 @@ SBH_API sbh_status sbh_eval(const sbh_tree* tree, const float* queries, int64_t 
                     int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
                     float* out, void* stream);
 
+/* The work sbh_eval does for the same arguments, counted instead of evaluated: the same paths
+ * are walked (same decisions) and no output is written. counts: device [4] unsigned 64-bit,
+ * accumulated into (the caller zeroes them): [0] kernel terms evaluated (control variates, every
+ * child of a swap and the swapped node), [1] node records read for those terms, [2] decisions
+ * (child pick + roulette, one Philox block each), [3] child prefix fractions read by the picks.
+ * Used to turn a measured time into achieved work for the roofline. */
+SBH_API sbh_status sbh_eval_count(const sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel,
+                                  int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
+                                  unsigned long long* counts, void* stream);
+
 /* Deterministic Barnes-Hut (Algorithm 1) on the 8-ary tree: a node is used whole when it is a
  * single point or ||q - p_a|| / |B_a| >= beta = 1 / theta (theta = 0 gives the exact sum).
  * warp_vote = 1 takes the decision jointly for the 32 queries of a warp (a node is opened when
@@ -166,6 +178,9 @@ SBH_API void sbh_tree_free(sbh_tree* tree);
 
 /* Message describing the calling thread's most recent failure ("" if none). */
 SBH_API const char* sbh_last_error(void);
+
+/* Number of CUDA kernels this library has launched in this process so far (host-side count). */
+SBH_API unsigned long long sbh_kernel_launches(void);
 
 /* SBH_VERSION of the loaded library. */
 SBH_API int32_t sbh_version(void);

@@ -22,9 +22,9 @@ import threading
 
 import numpy as np
 
-__all__ = ["SBHError", "Tree", "EvalOpts", "kernel", "load_library", "sbh_build", "sbh_eval", "sbh_eval_bh",
-           "sbh_eval_brute", "sbh_tree_info", "sbh_tree_export", "sbh_tree_free", "sbh_last_error", "sbh_version",
-           "KERNELS"]
+__all__ = ["SBHError", "Tree", "EvalOpts", "kernel", "load_library", "sbh_build", "sbh_eval", "sbh_eval_count",
+           "sbh_eval_bh", "sbh_eval_brute", "sbh_tree_info", "sbh_tree_export", "sbh_tree_free", "sbh_last_error",
+           "sbh_version", "sbh_kernel_launches", "KERNELS"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libsbh.so")
@@ -44,8 +44,9 @@ class _Kernel(C.Structure):
 
 
 class EvalOpts(C.Structure):
-    """sbh_eval_opts: sampling (0 mass, 1 count), rr (0 Eq. 5, 1 off, 2 half), seed_mode (0, 1)."""
-    _fields_ = [("sampling", C.c_int32), ("rr", C.c_int32), ("seed_mode", C.c_int32), ("reserved", C.c_int32)]
+    """sbh_eval_opts: sampling (0 mass, 1 count), rr (0 Eq. 5, 1 off, 2 half), seed_mode (0, 1),
+    raw_sum (smooth distance: 1 returns the estimated sum instead of the distance)."""
+    _fields_ = [("sampling", C.c_int32), ("rr", C.c_int32), ("seed_mode", C.c_int32), ("raw_sum", C.c_int32)]
 
 
 class _Meta(C.Structure):
@@ -79,13 +80,16 @@ def load_library():
         lib.sbh_last_error.restype = C.c_char_p
         lib.sbh_build.argtypes = [P, P, P, i64, i32, P, C.POINTER(P)]
         lib.sbh_eval.argtypes = [P, P, i64, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts), P, P]
+        lib.sbh_eval_count.argtypes = [P, P, i64, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts), P, P]
+        lib.sbh_kernel_launches.restype = C.c_ulonglong
         lib.sbh_eval_bh.argtypes = [P, P, i64, _Kernel, C.c_float, i32, P, P]
         lib.sbh_eval_brute.argtypes = [P, P, P, i64, P, i64, _Kernel, i32, P, P]
         lib.sbh_tree_info.argtypes = [P, i32, C.POINTER(_Meta)]
         lib.sbh_tree_export.argtypes = [P, i32, C.POINTER(_Export)]
         lib.sbh_tree_free.argtypes = [P]
         lib.sbh_tree_free.restype = None
-        for f in ("sbh_build", "sbh_eval", "sbh_eval_bh", "sbh_eval_brute", "sbh_tree_info", "sbh_tree_export"):
+        for f in ("sbh_build", "sbh_eval", "sbh_eval_count", "sbh_eval_bh", "sbh_eval_brute", "sbh_tree_info",
+                  "sbh_tree_export"):
             getattr(lib, f).restype = i32
         _lib = lib
         return lib
@@ -195,6 +199,28 @@ def sbh_eval(tree: Tree, queries, kernel="coulomb", samples_per_subdomain: int =
                         C.c_uint64(int(seed) & (2**64 - 1)), C.byref(opts) if opts is not None else None,
                         _dev(out, "out"), _stream(stream)))
     return out
+
+
+def sbh_eval_count(tree: Tree, queries, kernel="coulomb", samples_per_subdomain: int = 1, seed: int = 0,
+                   opts: EvalOpts | None = None, stream=None, softening: float = 1e-3, alpha: float = 200.0,
+                   affine=(0.0, 0.0, 0.0)) -> dict:
+    """Work sbh_eval does for these arguments (same paths), counted: kernel terms, node records,
+    decisions, prefix fractions read. Synchronises the stream."""
+    torch = _torch()
+    lib = load_library()
+    nq = int(queries.shape[0])
+    counts = torch.zeros(4, dtype=torch.int64, device=queries.device)
+    k = _kernel_arg(kernel, softening, alpha, affine)
+    _check(lib.sbh_eval_count(tree.handle, _dev(queries, "queries", 3), nq, k, int(samples_per_subdomain),
+                              C.c_uint64(int(seed) & (2**64 - 1)), C.byref(opts) if opts is not None else None,
+                              C.c_void_p(counts.data_ptr()), _stream(stream)))
+    c = counts.cpu().tolist()
+    return {"terms": c[0], "records": c[1], "decisions": c[2], "cdf_reads": c[3]}
+
+
+def sbh_kernel_launches() -> int:
+    """CUDA kernels launched by libsbh.so in this process so far."""
+    return int(load_library().sbh_kernel_launches())
 
 
 def sbh_eval_bh(tree: Tree, queries, kernel="coulomb", theta: float = 0.5, warp_vote: bool = True, out=None,

@@ -7,11 +7,17 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <new>
 
 #include "sbh.h"
 #include "sbh_build.cuh"
 #include "sbh_eval.cuh"
+
+namespace sbh {
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace sbh
 
 namespace {
 
@@ -152,7 +158,8 @@ sbh_status sbh_eval(const sbh_tree* tree, const float* queries, int64_t nq, sbh_
         return fail(SBH_EINVAL, "the winding-number kernel needs a tree built with normals");
     sbh_eval_opts o = {0, 0, 0, 0};
     if (opts) o = *opts;
-    if (o.sampling < 0 || o.sampling > 1 || o.rr < 0 || o.rr > 2 || o.seed_mode < 0 || o.seed_mode > 1 || o.reserved != 0)
+    if (o.sampling < 0 || o.sampling > 1 || o.rr < 0 || o.rr > 2 || o.seed_mode < 0 || o.seed_mode > 1 ||
+        o.raw_sum < 0 || o.raw_sum > 1)
         return fail(SBH_EINVAL, "sbh_eval_opts out of range");
     if (nq == 0) return SBH_OK;
     if (!device_ptr(queries) || !device_ptr(out)) return fail(SBH_EINVAL, "queries and out must be device memory");
@@ -161,6 +168,35 @@ sbh_status sbh_eval(const sbh_tree* tree, const float* queries, int64_t nq, sbh_
     if (e != cudaSuccess) return cuda_fail(e, "sbh_eval launch");
     return SBH_OK;
 }
+
+sbh_status sbh_eval_count(const sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel,
+                          int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
+                          unsigned long long* counts, void* stream)
+{
+    g_err[0] = 0;
+    if (!tree || !tree->t4.built) return fail(SBH_EINVAL, "tree is NULL or not built");
+    if (nq < 0) return fail(SBH_EINVAL, "nq < 0");
+    if (samples_per_subdomain < 1) return fail(SBH_EINVAL, "samples_per_subdomain must be >= 1");
+    sbh::KernelParams kp;
+    sbh_status st = check_kernel(kernel, &kp);
+    if (st != SBH_OK) return st;
+    if (kernel.kind == SBH_WINDING && !tree->has_normals)
+        return fail(SBH_EINVAL, "the winding-number kernel needs a tree built with normals");
+    sbh_eval_opts o = {0, 0, 0, 0};
+    if (opts) o = *opts;
+    if (o.sampling < 0 || o.sampling > 1 || o.rr < 0 || o.rr > 2 || o.seed_mode < 0 || o.seed_mode > 1 ||
+        o.raw_sum < 0 || o.raw_sum > 1)
+        return fail(SBH_EINVAL, "sbh_eval_opts out of range");
+    if (!device_ptr(counts)) return fail(SBH_EINVAL, "counts must be device memory");
+    if (nq == 0) return SBH_OK;
+    if (!device_ptr(queries)) return fail(SBH_EINVAL, "queries must be device memory");
+    cudaError_t e = sbh::launch_stoch_count(tree->t4.view(), queries, nq, kp, samples_per_subdomain, seed, o, counts,
+                                            (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_eval_count launch");
+    return SBH_OK;
+}
+
+unsigned long long sbh_kernel_launches(void) { return sbh::g_launches.load(std::memory_order_relaxed); }
 
 sbh_status sbh_eval_bh(sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel, float theta,
                        int32_t warp_vote, float* out, void* stream)

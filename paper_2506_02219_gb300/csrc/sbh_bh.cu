@@ -79,6 +79,7 @@ static void launch_bh_kind(const TreeView& T, const float* Q, int64_t nq, const 
 {
     if (vote) k_bh_eval<KIND, true><<<blocks, 256, 0, s>>>(T, Q, nq, kp, beta, out);
     else k_bh_eval<KIND, false><<<blocks, 256, 0, s>>>(T, Q, nq, kp, beta, out);
+    note_launch();
 }
 
 cudaError_t launch_bh_eval(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, float beta,

@@ -78,6 +78,7 @@ static void launch_brute_kind(const float* P, const float* W, const float* N, in
     const unsigned blocks = (unsigned)((nq + kBruteThreads - 1) / kBruteThreads);
     if (fp64) k_brute<KIND, true><<<blocks, kBruteThreads, 0, s>>>(P, W, N, n, Q, nq, kp, out);
     else k_brute<KIND, false><<<blocks, kBruteThreads, 0, s>>>(P, W, N, n, Q, nq, kp, out);
+    note_launch();
 }
 
 cudaError_t launch_brute(const float* P, const float* W, const float* N, int64_t n, const float* Q, int64_t nq,

@@ -267,13 +267,16 @@ void scan_exclusive(const int* in, int* out, int64_t n, int* temp, cudaStream_t 
     if (n <= 0) return;
     if (n <= kScanTile) {
         k_scan_tile<<<1, kScanThreads, 0, s>>>(in, n, nullptr, out);
+        note_launch();
         return;
     }
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     int* sums = temp;
     k_scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
+    note_launch();
     scan_exclusive(sums, sums, nb, temp + nb, s);
     k_scan_tile<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums, out);
+    note_launch();
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -695,7 +698,9 @@ cudaError_t build_sorted(sbh_tree* T, const float* pts, const float* w, const fl
     int* scratch = nullptr;
     SBH_TRY(dalloc((void**)&scratch, 8 * sizeof(int), s));
     k_bounds_init<<<1, 32, 0, s>>>(scratch);
+    note_launch();
     k_bounds<<<grid_for(n), kThreads, 0, s>>>(pts, w, n, scratch);
+    note_launch();
     int host[8];
     SBH_TRY(cudaMemcpyAsync(host, scratch, sizeof(host), cudaMemcpyDeviceToHost, s));
     SBH_TRY(cudaStreamSynchronize(s));
@@ -706,6 +711,7 @@ cudaError_t build_sorted(sbh_tree* T, const float* pts, const float* w, const fl
         return cudaSuccess;
     }
     k_root_cube<<<1, 32, 0, s>>>(scratch, T->t4.ctrl, T->t2.ctrl);
+    note_launch();
     SBH_TRY(cudaGetLastError());
     dfree(scratch, s);
 
@@ -721,11 +727,14 @@ cudaError_t build_sorted(sbh_tree* T, const float* pts, const float* w, const fl
     SBH_TRY(dalloc((void**)&hist, nhist * sizeof(int), s));
     SBH_TRY(dalloc((void**)&tmp, scan_temp_ints(nhist) * sizeof(int), s));
     k_morton<<<grid_for(n), kThreads, 0, s>>>(pts, n, T->t4.ctrl, k0, v0);
+    note_launch();
     for (int pass = 0; pass < 8; ++pass) {
         const int shift = 8 * pass;
         k_radix_hist<<<ntiles, kSortThreads, 0, s>>>(k0, n, shift, ntiles, hist);
+        note_launch();
         scan_exclusive(hist, hist, nhist, tmp, s);
         k_radix_scatter<<<ntiles, kSortThreads, 0, s>>>(k0, v0, n, shift, ntiles, hist, k1, v1);
+        note_launch();
         uint64_t* tk = k0; k0 = k1; k1 = tk;
         int32_t* tv = v0; v0 = v1; v1 = tv;
     }
@@ -742,7 +751,9 @@ cudaError_t build_sorted(sbh_tree* T, const float* pts, const float* w, const fl
     SBH_TRY(dalloc((void**)&T->lcp4, n, s));
     SBH_TRY(dalloc((void**)&T->lcp2, n, s));
     k_gather<<<grid_for(n), kThreads, 0, s>>>(pts, w, nrm, T->perm, n, T->spw, T->snrm);
+    note_launch();
     k_lcp<<<grid_for(n), kThreads, 0, s>>>(T->code, n, T->lcp4, T->lcp2);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -766,25 +777,40 @@ cudaError_t build_tree(sbh_tree* T, DeviceTree& D, const uint8_t* lcp, int max_l
 
     const unsigned g = grid_for(n);
     k_set_int<<<1, 32, 0, s>>>(rmin, 255);
+    note_launch();
     k_min_u8<<<g, kThreads, 0, s>>>(lcp, n, rmin);
+    note_launch();
     k_topo_root<<<1, 32, 0, s>>>(B, rmin);
+    note_launch();
     k_topo_seed<<<g, kThreads, 0, s>>>(B);
+    note_launch();
     const int generations = max_level + 2;  // levels strictly increase; points end one below the deepest level
     for (int gen = 0; gen < generations; ++gen) {
         k_topo_flags<<<g, kThreads, 0, s>>>(B);
+        note_launch();
         scan_exclusive(flag, scan, n, tmp, s);
         k_topo_children<<<g, kThreads, 0, s>>>(B, gen);
+        note_launch();
         k_topo_minlcp<<<g, kThreads, 0, s>>>(B, gen);
+        note_launch();
         k_topo_classify<<<g, kThreads, 0, s>>>(B, gen);
+        note_launch();
     }
     SBH_TRY(cudaGetLastError());
-    for (int gen = generations; gen >= 0; --gen)
+    for (int gen = generations; gen >= 0; --gen) {
         k_aggregate<<<grid_for(n), kThreads, 0, s>>>(D.fc, D.meta, D.nb, T->spw, T->snrm, D.ctrl, gen, D.agg);
+        note_launch();
+    }
     k_pack<<<grid_for(2 * n), kThreads, 0, s>>>(D.agg, D.fc, D.meta, D.ctrl, D.pm, D.dip, D.cdf);
+    note_launch();
     k_finalize<<<1, 32, 0, s>>>(D.ctrl, D.fc, D.meta);
-    if (with_skip)
-        for (int gen = 0; gen <= generations; ++gen)
+    note_launch();
+    if (with_skip) {
+        for (int gen = 0; gen <= generations; ++gen) {
             k_skip<<<grid_for(n), kThreads, 0, s>>>(D.parent, D.fc, D.meta, D.ctrl, gen, D.skip);
+            note_launch();
+        }
+    }
     SBH_TRY(cudaGetLastError());
     dfree(cid, s); dfree(flag, s); dfree(scan, s); dfree(tmp, s); dfree(rmin, s);
     D.built = true;

@@ -41,6 +41,12 @@ struct Terms {
 
 // sum_c m_c f(p_c, q) over the children [f, f + nc) of a node, minus m_T f(p_T, q), times w,
 // added to the running accumulator
+// work counters of one thread (compiled out unless COUNT): kernel terms evaluated, node records
+// read by swaps and control variates, decisions (one Philox block each), prefix fractions read
+struct Counters {
+    unsigned long long evals = 0, records = 0, decisions = 0, cdf_reads = 0;
+};
+
 template <int KIND>
 __device__ __forceinline__ void add_swap(const TreeView& T, int32_t node, int32_t f, int nc, float4 pT, float dT_fast,
                                          float3 q, const KernelParams& kp, float w, float& acc, ExpAcc& ex)
@@ -64,11 +70,13 @@ __device__ __forceinline__ void add_swap(const TreeView& T, int32_t node, int32_
     }
 }
 
-template <int KIND>
+template <int KIND, bool COUNT>
 __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __restrict__ Q, int64_t nq,
                                                     KernelParams kp, int S, uint2 key, int sampling, int rr,
-                                                    int coherent, float* __restrict__ out)
+                                                    int coherent, int raw_sum, float* __restrict__ out,
+                                                    unsigned long long* __restrict__ counts)
 {
+    Counters cnt;
     __shared__ float sdiam[kDiamLevels];
     if (threadIdx.x < kDiamLevels) sdiam[threadIdx.x] = T.ctrl->diam[threadIdx.x];
     __syncthreads();
@@ -94,6 +102,7 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
             } else {
                 acc += Terms<KIND>::value(T, a, pa, q, kp);
             }
+            if (COUNT) { cnt.evals += 1; cnt.records += 1; }
             if (meta_kind(ma) == kPoint) continue;
             // a's weight for p(I in T): aggregate mass or point count
             const float wa = sampling ? (float)(__ldg(&T.ne[a]) - __ldg(&T.nb[a])) : pa.w;
@@ -120,6 +129,7 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                         const int32_t target = b + (int32_t)(((uint64_t)(x.x >> 8) * (uint64_t)cnt) >> 24);
                         for (int k = 1; k < nc; ++k) pick += (__ldg(&T.nb[f + k]) <= target) ? 1 : 0;
                     }
+                    if (COUNT) { cnt.decisions += 1; cnt.cdf_reads += (uint64_t)(nc - 1); }
                     const int32_t c = f + pick;
                     const float4 pc = __ldg(&T.pm[c]);
                     const uint32_t mc = __ldg(&T.meta[c]);
@@ -132,6 +142,7 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                     const float pagg = wT / wa;
                     const float w = 1.0f / (pagg * prr) * invS;
                     add_swap<KIND>(T, node, f, nc, pT, dT_fast, q, kp, w, acc, ex);
+                    if (COUNT) { cnt.evals += (uint64_t)nc + 1; cnt.records += (uint64_t)nc; }
                     node = c;
                     pT = pc;
                     mT = mc;
@@ -141,39 +152,68 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                 }
             }
         }
+        if (COUNT) continue;
         if constexpr (KIND == SBH_SMOOTHDIST) {
-            out[j] = ex.acc > 0.0f ? ex.ref - __logf(ex.acc) / kp.alpha : __int_as_float(0x7F800000);
+            if (raw_sum) out[j] = ex.acc * __expf(-kp.alpha * ex.ref);
+            else out[j] = ex.acc > 0.0f ? ex.ref - __logf(ex.acc) / kp.alpha : __int_as_float(0x7F800000);
         } else {
             out[j] = acc;
         }
     }
+    if (COUNT) {
+        unsigned long long v[4] = {cnt.evals, cnt.records, cnt.decisions, cnt.cdf_reads};
+        for (int k = 0; k < 4; ++k) {
+            unsigned long long x = v[k];
+            for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, off);
+            if ((threadIdx.x & 31) == 0) atomicAdd(&counts[k], x);
+        }
+    }
 }
 
-cudaError_t launch_stoch_eval(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
-                              uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s)
+template <bool COUNT>
+static cudaError_t launch_stoch_impl(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
+                                     uint64_t seed, const sbh_eval_opts& o, float* out,
+                                     unsigned long long* counts, cudaStream_t s)
 {
     if (nq <= 0) return cudaSuccess;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     const int threads = 256;
     int64_t blocks = (nq + threads - 1) / threads;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (COUNT) {
+        if (blocks > 152 * 64) blocks = 152 * 64;  // whole warps keep looping for the final reduction
+    } else if (blocks > 152 * 64) {
+        blocks = 152 * 64;
+    }
     switch (kp.kind) {
     case SBH_COULOMB:
-        k_stoch_eval<SBH_COULOMB><<<(unsigned)blocks, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, out);
+        k_stoch_eval<SBH_COULOMB, COUNT><<<(unsigned)blocks, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, counts);
         break;
     case SBH_WINDING:
-        k_stoch_eval<SBH_WINDING><<<(unsigned)blocks, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, out);
+        k_stoch_eval<SBH_WINDING, COUNT><<<(unsigned)blocks, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, counts);
         break;
     case SBH_SMOOTHDIST:
-        k_stoch_eval<SBH_SMOOTHDIST><<<(unsigned)blocks, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, out);
+        k_stoch_eval<SBH_SMOOTHDIST, COUNT><<<(unsigned)blocks, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, counts);
         break;
     case SBH_AFFINE:
-        k_stoch_eval<SBH_AFFINE><<<(unsigned)blocks, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, out);
+        k_stoch_eval<SBH_AFFINE, COUNT><<<(unsigned)blocks, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, counts);
         break;
     default:
         return cudaErrorInvalidValue;
     }
+    note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_stoch_eval(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
+                              uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s)
+{
+    return launch_stoch_impl<false>(T, Q, nq, kp, S, seed, o, out, nullptr, s);
+}
+
+cudaError_t launch_stoch_count(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
+                               uint64_t seed, const sbh_eval_opts& o, unsigned long long* counts, cudaStream_t s)
+{
+    return launch_stoch_impl<true>(T, Q, nq, kp, S, seed, o, nullptr, counts, s);
 }
 
 }  // namespace sbh

@@ -12,6 +12,9 @@
 
 namespace sbh {
 
+// host-side count of kernel launches made by the library (reported by sbh_kernel_launches)
+void note_launch();
+
 // ----------------------------------------------------------------------------------------------
 // Limits
 // ----------------------------------------------------------------------------------------------

@@ -17,7 +17,12 @@ def parity_error(kind, gpu, ref, alpha=200.0):
     gpu = np.asarray(gpu, np.float64)
     ref = np.asarray(ref, np.float64)
     if kind == "smoothdist":
-        return np.abs(alpha * gpu + np.log(ref))  # gpu is -log(F_gpu)/alpha
+        # gpu is -log(F_gpu)/alpha, +inf where the estimate of F is <= 0
+        err = np.full(ref.shape, np.inf)
+        pos = ref > 0
+        err[pos] = np.abs(alpha * gpu[pos] + np.log(ref[pos]))
+        err[~pos & np.isposinf(gpu)] = 0.0
+        return err
     if kind == "winding":
         return np.abs(gpu - ref) / np.maximum(np.abs(ref), 1.0)
     return np.abs(gpu - ref) / np.abs(ref)
