@@ -10,18 +10,20 @@ def dev(a):
     return None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-def parity_error(kind, gpu, ref, alpha=200.0):
-    """Per-query error of a GPU estimate against an oracle value, in the units the tolerance uses:
-    relative for Coulomb / affine, relative to max(|F|, 1) for winding numbers, and for the smooth
-    distance the difference of log F (= alpha * distance), i.e. the relative error of the sum."""
+def parity_error(kind, gpu, ref, alpha=200.0, exact=None):
+    """Per-query error of a GPU estimate against the oracle's replay of the same random stream, in
+    the units the tolerance uses: relative for Coulomb / affine, relative to max(|F|, 1) for winding
+    numbers. For the smooth distance the GPU returns d = -log(F_gpu) / alpha (+inf where its
+    estimate of F is <= 0); the error is |F_gpu - F_oracle| / F_exact, the estimate's error relative
+    to the exact sum (the estimate itself may cancel to near zero or below), and an output of +inf
+    matches an oracle estimate <= 0."""
     gpu = np.asarray(gpu, np.float64)
     ref = np.asarray(ref, np.float64)
     if kind == "smoothdist":
-        # gpu is -log(F_gpu)/alpha, +inf where the estimate of F is <= 0
-        err = np.full(ref.shape, np.inf)
-        pos = ref > 0
-        err[pos] = np.abs(alpha * gpu[pos] + np.log(ref[pos]))
-        err[~pos & np.isposinf(gpu)] = 0.0
+        assert exact is not None, "the smooth-distance error is relative to the exact sum"
+        Fg = np.where(np.isposinf(gpu), 0.0, np.exp(-alpha * gpu))
+        err = np.abs(Fg - ref) / np.asarray(exact, np.float64)
+        err[np.isposinf(gpu) & (ref <= 0)] = 0.0
         return err
     if kind == "winding":
         return np.abs(gpu - ref) / np.maximum(np.abs(ref), 1.0)

@@ -45,8 +45,10 @@ def test_estimator_matches_replay(sbh, oracle_mod, kind, S, leaf):
     t = sbh.sbh_build(dev(pts), dev(w), dev(nrm), leaf_size=leaf)
     seed = 0x5BA7 + S
     g = sbh.sbh_eval(t, dev(q), samples_per_subdomain=S, seed=seed, **gpu_kwargs(kind)).cpu().numpy()
-    o = oracle_mod.Tree(pts, w, nrm, leaf_size=leaf, d=4).replay(q, S=S, seed=seed, **oracle_kwargs(oracle_mod, kind))
-    err = parity_error(kind, g, o)
+    kw = oracle_kwargs(oracle_mod, kind)
+    o = oracle_mod.Tree(pts, w, nrm, leaf_size=leaf, d=4).replay(q, S=S, seed=seed, **kw)
+    exact = oracle_mod.brute(pts, w, q, normals=nrm, **kw) if kind == "smoothdist" else None
+    err = parity_error(kind, g, o, exact=exact)
     assert np.mean(err <= TOL) >= 0.999, (np.sort(err)[-10:], np.mean(err <= TOL))
 
 
@@ -88,8 +90,10 @@ def test_bh_matches_algorithm_1(sbh, oracle_mod, kind, theta):
     t = sbh.sbh_build(dev(pts), dev(w), dev(nrm))
     g = sbh.sbh_eval_bh(t, dev(q), theta=theta, warp_vote=False, **gpu_kwargs(kind)).cpu().numpy()
     beta = float(np.float32(1.0) / np.float32(theta))
-    o = oracle_mod.Tree(pts, w, nrm, leaf_size=1, d=2).bh(q, beta, **oracle_kwargs(oracle_mod, kind))
-    err = parity_error(kind, g, o)
+    kw = oracle_kwargs(oracle_mod, kind)
+    o = oracle_mod.Tree(pts, w, nrm, leaf_size=1, d=2).bh(q, beta, **kw)
+    exact = oracle_mod.brute(pts, w, q, normals=nrm, **kw) if kind == "smoothdist" else None
+    err = parity_error(kind, g, o, exact=exact)
     assert np.mean(err <= 1e-4) >= 0.999, np.sort(err)[-5:]
 
 
@@ -113,8 +117,8 @@ def test_brute_matches_oracle(sbh, oracle_mod, kind, fp64):
     F = oracle_mod.brute(pts, w, q, normals=nrm, **kw)
     g = sbh.sbh_eval_brute(dev(pts), dev(w), dev(q), normals=dev(nrm), fp64_accum=fp64,
                            **gpu_kwargs(kind)).cpu().numpy()
-    err = parity_error(kind, g, F)
+    err = parity_error(kind, g, F, exact=F)
     # smooth distance: each FP32 distance carries ~1e-7 relative error, which alpha = 200 turns
-    # into ~2e-5 in each exponent, hence in log F
+    # into ~2e-5 in each exponent, hence in the sum
     tol = (5e-5 if kind == "smoothdist" else 2e-6) if fp64 else 1e-4
     assert np.max(err) < tol, np.max(err)
