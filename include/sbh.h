@@ -179,6 +179,25 @@ SBH_API void sbh_tree_free(sbh_tree* tree);
 /* Message describing the calling thread's most recent failure ("" if none). */
 SBH_API const char* sbh_last_error(void);
 
+/* Allocation-free Morton ordering. The paper has no counterpart: this serves callers that cannot
+ * allocate device memory -- real-time loops that cannot afford the implicit synchronisation of an
+ * allocation, and applications that give the library a fixed memory budget and own every
+ * allocation. It computes the same 60-bit codes and the same stable order sbh_build uses (what
+ * sbh_tree_export reports as `code` and `perm`) without calling cudaMalloc, cudaFree or any
+ * allocating routine.
+ *   points  device [n][3], finite (not checked: a check would need a device-to-host read)
+ *   codes   device [n] out: sorted codes;  perm device [n] out: input index of each sorted point
+ *   n       1 <= n <= SBH_NOALLOC_MAX_POINTS; larger n returns SBH_EINVAL with a message
+ * Scratch lives in one static device array of about 0.8 MB that every GPU loading the library
+ * holds until the process exits; all calls share it and it keeps the last call's contents, so
+ * calls whose GPU work overlaps (on different streams, or from different threads) race and must
+ * be ordered by the caller. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any stream
+ * capture. Enqueued on `stream`, no synchronisation. */
+#define SBH_NOALLOC_MAX_POINTS 65536
+SBH_API sbh_status sbh_morton_sort_noalloc(const float* points, int64_t n, uint64_t* codes, int32_t* perm,
+                                           void* stream);
+
 /* Number of CUDA kernels this library has launched in this process so far (host-side count). */
 SBH_API unsigned long long sbh_kernel_launches(void);
 

@@ -32,6 +32,18 @@ sbh_status fail(sbh_status st, const char* fmt, ...)
     return st;
 }
 
+}  // namespace
+
+void sbh::set_error_message(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+namespace {
+
 sbh_status cuda_fail(cudaError_t e, const char* what)
 {
     const sbh_status st = (e == cudaErrorMemoryAllocation) ? SBH_ENOMEM : SBH_ECUDA;

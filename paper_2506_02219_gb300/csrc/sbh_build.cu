@@ -19,6 +19,7 @@
 #include <stdint.h>
 
 #include "sbh_build.cuh"
+#include "sbh_sort.cuh"
 
 namespace sbh {
 
@@ -286,10 +287,6 @@ void scan_exclusive(const int* in, int* out, int64_t n, int* temp, cudaStream_t 
 //    one-bit splits of (digit, slot) words in shared memory; the ninth moves padding last),
 //    then each key goes to offset[digit][tile] + its rank among the tile's keys of that digit.
 // ----------------------------------------------------------------------------------------------
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 8;
-constexpr int kSortTile = kSortThreads * kSortItems;
-
 __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint64_t* __restrict__ keys, int64_t n,
                                                              int shift, int ntiles, int* __restrict__ hist)
 {

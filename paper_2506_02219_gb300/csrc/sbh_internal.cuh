@@ -14,6 +14,8 @@ namespace sbh {
 
 // host-side count of kernel launches made by the library (reported by sbh_kernel_launches)
 void note_launch();
+// set the calling thread's sbh_last_error() message (printf-style)
+void set_error_message(const char* fmt, ...);
 
 // ----------------------------------------------------------------------------------------------
 // Limits
