@@ -80,7 +80,7 @@ def _load():
         lib.sbho_tree_meta.argtypes = [P, P, P]
         lib.sbho_tree_export.argtypes = [P] + [P] * 11
         lib.sbho_bh.argtypes = [P, C.POINTER(_Kernel), P, i64, C.c_float, P]
-        lib.sbho_replay.argtypes = [P, C.POINTER(_Kernel), P, i64, i32, u64, C.POINTER(_Opts), P, P, P]
+        lib.sbho_replay.argtypes = [P, C.POINTER(_Kernel), P, i64, i32, u64, C.POINTER(_Opts), P, P, P, P]
         lib.sbho_enumerate.argtypes = [P, C.POINTER(_Kernel), P, i64, C.POINTER(_Opts), P, P]
         lib.sbho_max_threads.restype = i32
         lib.sbho_set_threads.argtypes = [i32]
@@ -197,19 +197,27 @@ class Tree:
 
     def replay(self, queries, S: int = 1, seed: int = 0, kind=COULOMB, softening=1e-3, alpha=200.0,
                affine=(0.0, 0.0, 0.0), sampling=SAMPLE_MASS, rr=RR_PAPER, coherent=False,
-               return_swaps=False, query_index=None):
+               return_swaps=False, query_index=None, return_abs_sum=False):
         """Algorithm 2 replayed with the Philox stream; returns the FP64 estimate of the kernel
         sum per query (the sum of exponentials for the smooth distance kernel). query_index gives
-        each query's index in the random stream (default: its position)."""
+        each query's index in the random stream (default: its position). With return_abs_sum the
+        sum of the absolute values of all terms the estimate adds is returned too (the scale of
+        the rounding error of any evaluation of the same signed sum)."""
         q = _f32(queries, 3)
         qidx = None if query_index is None else np.ascontiguousarray(np.asarray(query_index, dtype=np.uint32))
         out = np.zeros(q.shape[0], np.float64)
         swaps = np.zeros(q.shape[0], np.int64)
         k = kernel(kind, softening, alpha, affine)
         o = _opts(sampling, rr, coherent)
+        absum = np.zeros(q.shape[0], np.float64)
         self._lib.sbho_replay(self._h, C.byref(k), _ptr(q), q.shape[0], int(S), C.c_uint64(seed & (2**64 - 1)),
-                              C.byref(o), _ptr(qidx), _ptr(out), _ptr(swaps))
-        return (out, swaps) if return_swaps else out
+                              C.byref(o), _ptr(qidx), _ptr(out), _ptr(swaps), _ptr(absum))
+        res = (out,)
+        if return_swaps:
+            res += (swaps,)
+        if return_abs_sum:
+            res += (absum,)
+        return res if len(res) > 1 else out
 
     def enumerate(self, queries, kind=COULOMB, softening=1e-3, alpha=200.0, affine=(0.0, 0.0, 0.0),
                   sampling=SAMPLE_MASS, rr=RR_PAPER):

@@ -531,6 +531,16 @@ static double swap_delta(const otree *t, const sbho_kernel *k, int64_t v, const 
     return s - node_term(t, k, v, q);
 }
 
+/* Magnitude of a swap's terms: sum over children of |m_c f(p_c, q)| plus |m_v f(p_v, q)|. The
+ * replay adds these (with the same weights) into abs_sum, the scale against which a computation
+ * in lower precision of the same signed sum can be compared. */
+static double swap_abs(const otree *t, const sbho_kernel *k, int64_t v, const double q[3])
+{
+    double s = 0;
+    for (int c = 0; c < t->nchild[v]; ++c) s += fabs(node_term(t, k, t->first_child[v] + c, q));
+    return s + fabs(node_term(t, k, v, q));
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Barnes-Hut, Algorithm 1: stop at a leaf or when beta~ >= beta, else recurse into children.   */
 /* The far-field test is taken in FP32 (beta~ as above); sums are FP64.                        */
@@ -559,6 +569,7 @@ SBHO_API void sbho_bh(const void *h, const sbho_kernel *k, const float *queries,
 /* ------------------------------------------------------------------------------------------ */
 /* Algorithm 2 (stratified path sample estimator), replayed with the Philox stream.             */
 /* The counter's query index is qidx[j] when given (queries drawn from a larger set), else j.  */
+/* abs_sum[j] (optional) gets the sum of the absolute values of every term the estimate adds.   */
 /*   for each subdomain a (children of the root, Sec. 3.3.1):                                  */
 /*     CV_a = m_a f(p_a, q);  F_a = 0                                                          */
 /*     for s in 1..S: T = a, k = 0, p_rr = 1                                                   */
@@ -579,7 +590,7 @@ typedef struct {
 
 SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *queries, int64_t nq,
                           int32_t S, uint64_t seed, const sbho_opts *opts, const uint32_t *qidx,
-                          double *out, int64_t *nswaps)
+                          double *out, int64_t *nswaps, double *abs_sum)
 {
     const otree *t = (const otree *)h;
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
@@ -590,12 +601,12 @@ SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *quer
     for (int64_t j = 0; j < nq; ++j) {
         float q32[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
         double q[3] = {q32[0], q32[1], q32[2]};
-        double F = 0;
+        double F = 0, A = 0;
         int64_t swaps = 0;
         for (int64_t ai = 0; ai < t->n_sub; ++ai) {
             int64_t a = t->first_sub + ai;
             double CV = node_term(t, k, a, q);
-            double Fa = 0;
+            double Fa = 0, Aa = 0;
             for (int32_t s = 0; s < S; ++s) {
                 int64_t T = a;
                 uint32_t depth = 0;
@@ -611,15 +622,18 @@ SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *quer
                     double pagg = p_in(t, T, a, sampling);
                     prr *= (double)p;
                     Fa += delta / (pagg * prr);
+                    Aa += swap_abs(t, k, T, q) / (pagg * prr);
                     ++swaps;
                     T = c;
                     ++depth;
                 }
             }
             F += CV + Fa / (double)S;
+            A += fabs(CV) + Aa / (double)S;
         }
         out[j] = F;
         if (nswaps) nswaps[j] = swaps;
+        if (abs_sum) abs_sum[j] = A;
     }
 }
 

@@ -10,21 +10,29 @@ def dev(a):
     return None if a is None else torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
 
 
-def parity_error(kind, gpu, ref, alpha=200.0, exact=None):
-    """Per-query error of a GPU estimate against the oracle's replay of the same random stream, in
-    the units the tolerance uses: relative for Coulomb / affine, relative to max(|F|, 1) for winding
-    numbers. For the smooth distance the GPU returns d = -log(F_gpu) / alpha (+inf where its
-    estimate of F is <= 0); the error is |F_gpu - F_oracle| / F_exact, the estimate's error relative
-    to the exact sum (the estimate itself may cancel to near zero or below), and an output of +inf
-    matches an oracle estimate <= 0."""
+def parity_error(kind, gpu, ref, abs_sum, alpha=200.0):
+    """Per-query error of a GPU estimate against the oracle's replay of the same random stream:
+    |F_gpu - F_oracle| / A, with A the sum of the absolute values of every term the estimate adds
+    (the oracle's abs_sum; A >= |F|, and A is the scale of the rounding error of any evaluation of
+    the same signed sum), at least 1 for winding numbers. For the smooth distance the GPU returns
+    d = -log(F_gpu) / alpha, +inf where its estimate of F is <= 0 (F_gpu = 0 here)."""
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    scale = np.asarray(abs_sum, np.float64)
+    if kind == "smoothdist":
+        gpu = np.where(np.isposinf(gpu), 0.0, np.exp(-alpha * gpu))
+    if kind == "winding":
+        scale = np.maximum(scale, 1.0)
+    return np.abs(gpu - ref) / scale
+
+
+def rel_error(kind, gpu, ref, alpha=200.0):
+    """Plain error against an exact value: relative for Coulomb / affine, relative to max(|F|, 1)
+    for winding numbers, and for the smooth distance relative error of the sum exp(-alpha d)."""
     gpu = np.asarray(gpu, np.float64)
     ref = np.asarray(ref, np.float64)
     if kind == "smoothdist":
-        assert exact is not None, "the smooth-distance error is relative to the exact sum"
-        Fg = np.where(np.isposinf(gpu), 0.0, np.exp(-alpha * gpu))
-        err = np.abs(Fg - ref) / np.asarray(exact, np.float64)
-        err[np.isposinf(gpu) & (ref <= 0)] = 0.0
-        return err
+        return np.abs(np.exp(-alpha * gpu) - ref) / ref
     if kind == "winding":
         return np.abs(gpu - ref) / np.maximum(np.abs(ref), 1.0)
     return np.abs(gpu - ref) / np.abs(ref)

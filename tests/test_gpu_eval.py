@@ -1,9 +1,9 @@
 """GPU evaluation kernels against the oracle on the same seeded inputs.
 
 - sbh_eval vs the oracle's replay of Algorithm 2 with the same Philox stream: per-query
-  estimates within 1e-4 (relative; for winding numbers relative to max(|F|, 1); for the smooth
-  distance on log F) on at least 99.9% of queries. Decisions are FP32 on both sides, so nearly
-  every query follows the same paths.
+  estimates within 1e-4 relative to the magnitude of their terms (|F_gpu - F_oracle| <= 1e-4 A,
+  A = sum of |terms| >= |F|) on at least 99.9% of queries. Decisions are FP32 on both sides, so
+  nearly every query follows the same paths.
 - seed-averaged GPU estimates within 3 sigma of the exact sum, sigma from the oracle's
   enumerated variance.
 - sbh_eval_bh without warp voting vs the oracle's Algorithm 1 (identical FP32 far-field
@@ -13,7 +13,7 @@
 import numpy as np
 import pytest
 
-from gpu_util import dev, gpu_kwargs, oracle_kwargs, parity_error
+from gpu_util import dev, gpu_kwargs, oracle_kwargs, parity_error, rel_error
 
 pytestmark = pytest.mark.gpu
 
@@ -46,9 +46,8 @@ def test_estimator_matches_replay(sbh, oracle_mod, kind, S, leaf):
     seed = 0x5BA7 + S
     g = sbh.sbh_eval(t, dev(q), samples_per_subdomain=S, seed=seed, **gpu_kwargs(kind)).cpu().numpy()
     kw = oracle_kwargs(oracle_mod, kind)
-    o = oracle_mod.Tree(pts, w, nrm, leaf_size=leaf, d=4).replay(q, S=S, seed=seed, **kw)
-    exact = oracle_mod.brute(pts, w, q, normals=nrm, **kw) if kind == "smoothdist" else None
-    err = parity_error(kind, g, o, exact=exact)
+    o, A = oracle_mod.Tree(pts, w, nrm, leaf_size=leaf, d=4).replay(q, S=S, seed=seed, return_abs_sum=True, **kw)
+    err = parity_error(kind, g, o, A)
     assert np.mean(err <= TOL) >= 0.999, (np.sort(err)[-10:], np.mean(err <= TOL))
 
 
@@ -59,8 +58,9 @@ def test_estimator_options_match_replay(sbh, oracle_mod, sampling, rr, coherent)
     o = sbh.EvalOpts()
     o.sampling, o.rr, o.seed_mode = sampling, rr, coherent
     g = sbh.sbh_eval(t, dev(q), "coulomb", seed=99, opts=o).cpu().numpy()
-    r = oracle_mod.Tree(pts, w).replay(q, S=1, seed=99, sampling=sampling, rr=rr, coherent=bool(coherent))
-    err = parity_error("coulomb", g, r)
+    r, A = oracle_mod.Tree(pts, w).replay(q, S=1, seed=99, sampling=sampling, rr=rr, coherent=bool(coherent),
+                                          return_abs_sum=True)
+    err = parity_error("coulomb", g, r, A)
     assert np.mean(err <= TOL) >= 0.999
 
 
@@ -92,8 +92,7 @@ def test_bh_matches_algorithm_1(sbh, oracle_mod, kind, theta):
     beta = float(np.float32(1.0) / np.float32(theta))
     kw = oracle_kwargs(oracle_mod, kind)
     o = oracle_mod.Tree(pts, w, nrm, leaf_size=1, d=2).bh(q, beta, **kw)
-    exact = oracle_mod.brute(pts, w, q, normals=nrm, **kw) if kind == "smoothdist" else None
-    err = parity_error(kind, g, o, exact=exact)
+    err = rel_error(kind, g, o)  # Barnes-Hut sums positive-weight terms: plainly relative
     assert np.mean(err <= 1e-4) >= 0.999, np.sort(err)[-5:]
 
 
@@ -117,7 +116,7 @@ def test_brute_matches_oracle(sbh, oracle_mod, kind, fp64):
     F = oracle_mod.brute(pts, w, q, normals=nrm, **kw)
     g = sbh.sbh_eval_brute(dev(pts), dev(w), dev(q), normals=dev(nrm), fp64_accum=fp64,
                            **gpu_kwargs(kind)).cpu().numpy()
-    err = parity_error(kind, g, F, exact=F)
+    err = rel_error(kind, g, F)
     # smooth distance: each FP32 distance carries ~1e-7 relative error, which alpha = 200 turns
     # into ~2e-5 in each exponent, hence in the sum
     tol = (5e-5 if kind == "smoothdist" else 2e-6) if fp64 else 1e-4

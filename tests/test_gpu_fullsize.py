@@ -31,13 +31,9 @@ def _check(sbh, oracle_mod, wl, kind, S, seed, tree=None, otree=None):
     out = sbh.sbh_eval(t, dev(wl.queries), samples_per_subdomain=S, seed=seed, **gpu_kwargs(kind)).cpu().numpy()
     idx = np.sort(np.random.default_rng(seed).choice(wl.queries.shape[0], N_SAMPLE, replace=False))
     ot = otree or oracle_mod.Tree(wl.points, wl.weights, wl.normals, leaf_size=1, d=4)
-    ref = ot.replay(wl.queries[idx], S=S, seed=seed, query_index=idx, **oracle_kwargs(oracle_mod, kind))
-    exact = None
-    if kind == "smoothdist":  # the scale of the error: the exact sum, from the FP64-accumulated brute force
-        d = sbh.sbh_eval_brute(dev(wl.points), dev(wl.weights), dev(wl.queries[idx]), normals=None, fp64_accum=True,
-                               **gpu_kwargs(kind)).cpu().numpy().astype(np.float64)
-        exact = np.exp(-200.0 * d)
-    err = parity_error(kind, out[idx], ref, exact=exact)
+    ref, A = ot.replay(wl.queries[idx], S=S, seed=seed, query_index=idx, return_abs_sum=True,
+                       **oracle_kwargs(oracle_mod, kind))
+    err = parity_error(kind, out[idx], ref, A)
     assert np.mean(err <= 1e-4) >= 0.999, (np.sort(err)[-8:], np.mean(err <= 1e-4))
     assert np.all(np.isfinite(out))
     return t, ot

@@ -142,3 +142,17 @@ def test_barnes_hut_error_shrinks_with_beta(oracle_mod):
     errs = [np.mean(np.abs(t.bh(q, b) - F) / F) for b in (1.0, 2.0, 4.0, 8.0)]
     assert all(errs[i + 1] < errs[i] for i in range(3)), errs
     assert errs[1] < 1e-2
+
+
+def test_abs_sum_bounds_the_estimate(oracle_mod):
+    """The replay's abs_sum (sum of |terms| the estimate adds) is >= |estimate|, equals the
+    estimate when every term is positive (subdomains that are points, Coulomb), and scales with S."""
+    t, q, F, kw = _setup(oracle_mod, 300, 14, "smoothdist")
+    est, A = t.replay(q, S=2, seed=4, return_abs_sum=True, **kw)
+    assert np.all(A >= np.abs(est) * (1 - 1e-12))
+    g = (np.arange(4) + 0.5) / 4
+    pts = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3).astype(np.float32)
+    w = np.full(64, 0.7, np.float32)
+    tp = oracle_mod.Tree(pts, w, d=4)
+    est, A = tp.replay(q, seed=1, return_abs_sum=True)
+    np.testing.assert_allclose(A, est, rtol=1e-14)
