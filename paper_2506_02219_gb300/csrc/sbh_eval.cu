@@ -14,6 +14,10 @@
 //
 // Decisions (child pick, roulette) are taken in FP32 with correctly rounded operations in a fixed
 // order; kernel values use fast FP32 arithmetic.
+//
+// This file's kernel walks each query's paths one lane per query; it is the counting variant
+// behind sbh_eval_count (same paths, same decisions). sbh_eval itself runs the batched schedule of
+// sbh_eval_batched.cu, which evaluates the same terms.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -179,11 +183,7 @@ static cudaError_t launch_stoch_impl(const TreeView& T, const float* Q, int64_t 
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     const int threads = 256;
     int64_t blocks = (nq + threads - 1) / threads;
-    if (COUNT) {
-        if (blocks > 152 * 64) blocks = 152 * 64;  // whole warps keep looping for the final reduction
-    } else if (blocks > 152 * 64) {
-        blocks = 152 * 64;
-    }
+    if (blocks > 152 * 64) blocks = 152 * 64;
     switch (kp.kind) {
     case SBH_COULOMB:
         k_stoch_eval<SBH_COULOMB, COUNT><<<(unsigned)blocks, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, counts);
@@ -207,7 +207,7 @@ static cudaError_t launch_stoch_impl(const TreeView& T, const float* Q, int64_t 
 cudaError_t launch_stoch_eval(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
                               uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s)
 {
-    return launch_stoch_impl<false>(T, Q, nq, kp, S, seed, o, out, nullptr, s);
+    return launch_stoch_batched(T, Q, nq, kp, S, seed, o, out, s);
 }
 
 cudaError_t launch_stoch_count(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,

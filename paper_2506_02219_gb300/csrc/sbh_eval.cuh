@@ -11,6 +11,9 @@ namespace sbh {
 cudaError_t launch_stoch_eval(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
                               uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s);
 
+cudaError_t launch_stoch_batched(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
+                                 uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s);
+
 cudaError_t launch_stoch_count(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
                                uint64_t seed, const sbh_eval_opts& o, unsigned long long* counts, cudaStream_t s);
 
