@@ -15,15 +15,20 @@ def parity_error(kind, gpu, ref, abs_sum, alpha=200.0):
     |F_gpu - F_oracle| / A, with A the sum of the absolute values of every term the estimate adds
     (the oracle's abs_sum; A >= |F|, and A is the scale of the rounding error of any evaluation of
     the same signed sum), at least 1 for winding numbers. For the smooth distance the GPU returns
-    d = -log(F_gpu) / alpha, +inf where its estimate of F is <= 0 (F_gpu = 0 here)."""
+    d = -log(F_gpu) / alpha, +inf where its estimate of F is <= 0; that matches an oracle estimate
+    <= 0."""
     gpu = np.asarray(gpu, np.float64)
     ref = np.asarray(ref, np.float64)
     scale = np.asarray(abs_sum, np.float64)
+    inf_out = np.isposinf(gpu)
     if kind == "smoothdist":
-        gpu = np.where(np.isposinf(gpu), 0.0, np.exp(-alpha * gpu))
+        gpu = np.where(inf_out, 0.0, np.exp(-alpha * gpu))
     if kind == "winding":
         scale = np.maximum(scale, 1.0)
-    return np.abs(gpu - ref) / scale
+    err = np.abs(gpu - ref) / scale
+    if kind == "smoothdist":  # a non-positive estimate has no distance: +inf matches any oracle estimate <= 0
+        err[inf_out & (ref <= 0)] = 0.0
+    return err
 
 
 def rel_error(kind, gpu, ref, alpha=200.0):
