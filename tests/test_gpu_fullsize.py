@@ -35,7 +35,8 @@ def _check(sbh, oracle_mod, wl, kind, S, seed, tree=None, otree=None):
                        **oracle_kwargs(oracle_mod, kind))
     err = parity_error(kind, out[idx], ref, A)
     assert np.mean(err <= 1e-4) >= 0.999, (np.sort(err)[-8:], np.mean(err <= 1e-4))
-    assert np.all(np.isfinite(out))
+    # +inf is the smooth distance of a non-positive estimate of the sum; nothing else may be non-finite
+    assert np.all(np.isfinite(out) | ((kind == "smoothdist") & np.isposinf(out)))
     return t, ot
 
 
