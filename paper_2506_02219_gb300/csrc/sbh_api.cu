@@ -141,14 +141,13 @@ sbh_status sbh_build(const float* points, const float* weights, const float* nor
         release(T, s);
         return cuda_fail(e, "sbh_build tree");
     }
-    int32_t build_error = 0;
-    e = cudaMemcpyAsync(&build_error, &T->t4.ctrl->error, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    e = cudaMemcpyAsync(&T->host_ctrl4, T->t4.ctrl, sizeof(sbh::TreeCtrl), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         release(T, s);
         return cuda_fail(e, "sbh_build");
     }
-    if (build_error) {
+    if (T->host_ctrl4.error) {
         release(T, s);
         return fail(SBH_EUNSUPPORTED, "sbh_build: more than 2^24 - 1 points share one deepest-level cell");
     }
@@ -175,8 +174,8 @@ sbh_status sbh_eval(const sbh_tree* tree, const float* queries, int64_t nq, sbh_
         return fail(SBH_EINVAL, "sbh_eval_opts out of range");
     if (nq == 0) return SBH_OK;
     if (!device_ptr(queries) || !device_ptr(out)) return fail(SBH_EINVAL, "queries and out must be device memory");
-    cudaError_t e = sbh::launch_stoch_eval(tree->t4.view(), queries, nq, kp, samples_per_subdomain, seed, o, out,
-                                           (cudaStream_t)stream);
+    cudaError_t e = sbh::launch_stoch_eval(tree->t4.view(), tree->host_ctrl4, queries, nq, kp, samples_per_subdomain,
+                                           seed, o, out, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "sbh_eval launch");
     return SBH_OK;
 }

@@ -60,6 +60,7 @@ struct sbh_tree {
     uint8_t* lcp2 = nullptr;         // the same, 3-bit digits
     sbh::DeviceTree t4;              // 64-ary tree (estimator)
     sbh::DeviceTree t2;              // 8-ary tree (Barnes-Hut), built on demand
+    sbh::TreeCtrl host_ctrl4;        // host copy of t4.ctrl, read when sbh_build finishes
 };
 
 namespace sbh {

@@ -204,10 +204,11 @@ static cudaError_t launch_stoch_impl(const TreeView& T, const float* Q, int64_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_stoch_eval(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
-                              uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s)
+cudaError_t launch_stoch_eval(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
+                              const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
+                              cudaStream_t s)
 {
-    return launch_stoch_batched(T, Q, nq, kp, S, seed, o, out, s);
+    return launch_stoch_batched(T, host_ctrl, Q, nq, kp, S, seed, o, out, s);
 }
 
 cudaError_t launch_stoch_count(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,

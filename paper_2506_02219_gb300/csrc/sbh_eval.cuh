@@ -8,11 +8,14 @@
 
 namespace sbh {
 
-cudaError_t launch_stoch_eval(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
-                              uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s);
+// host_ctrl: the host copy of the tree's control block (node counts per generation)
+cudaError_t launch_stoch_eval(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
+                              const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
+                              cudaStream_t s);
 
-cudaError_t launch_stoch_batched(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
-                                 uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s);
+cudaError_t launch_stoch_batched(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
+                                 const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
+                                 cudaStream_t s);
 
 cudaError_t launch_stoch_count(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
                                uint64_t seed, const sbh_eval_opts& o, unsigned long long* counts, cudaStream_t s);

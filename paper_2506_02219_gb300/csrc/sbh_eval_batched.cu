@@ -48,30 +48,83 @@ struct WarpState {
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << lane_id()) - 1u; }
 
+// The subdomains and their children (node generations 1 and 2) are read by every query: each
+// block copies them (up to kStageMax nodes) into shared memory at start and reads them there.
+constexpr int kStageMax = 2048;
+
+struct Stage {
+    int32_t lo;       // first staged node id
+    uint32_t n;       // number of staged nodes
+    float4* pm;
+    float4* dip;      // winding kernel only
+    float* cdf;
+    uint32_t* meta;
+    int32_t* fc;
+};
+
+__device__ __forceinline__ float4 ld_pm(const TreeView& T, const Stage& S, int32_t v)
+{
+    const uint32_t i = (uint32_t)(v - S.lo);
+    return i < S.n ? S.pm[i] : __ldg(&T.pm[v]);
+}
+__device__ __forceinline__ float4 ld_dip(const TreeView& T, const Stage& S, int32_t v)
+{
+    const uint32_t i = (uint32_t)(v - S.lo);
+    return i < S.n ? S.dip[i] : __ldg(&T.dip[v]);
+}
+__device__ __forceinline__ float ld_cdf(const TreeView& T, const Stage& S, int32_t v)
+{
+    const uint32_t i = (uint32_t)(v - S.lo);
+    return i < S.n ? S.cdf[i] : __ldg(&T.cdf[v]);
+}
+__device__ __forceinline__ uint32_t ld_meta(const TreeView& T, const Stage& S, int32_t v)
+{
+    const uint32_t i = (uint32_t)(v - S.lo);
+    return i < S.n ? S.meta[i] : __ldg(&T.meta[v]);
+}
+__device__ __forceinline__ int32_t ld_fc(const TreeView& T, const Stage& S, int32_t v)
+{
+    const uint32_t i = (uint32_t)(v - S.lo);
+    return i < S.n ? S.fc[i] : __ldg(&T.fc[v]);
+}
+
 // m f(p, q) of a node record (not used for the smooth distance, which works in exp frames)
 template <int KIND>
-__device__ __forceinline__ float node_value(const TreeView& T, int32_t v, float4 pm, float3 q, const KernelParams& kp)
+__device__ __forceinline__ float node_value(const TreeView& T, const Stage& S, int32_t v, float4 pm, float3 q,
+                                            const KernelParams& kp)
 {
     if constexpr (KIND == SBH_COULOMB) return term_coulomb(pm, q, kp.eps2);
-    else if constexpr (KIND == SBH_WINDING) return term_winding(pm, __ldg(&T.dip[v]), q);
+    else if constexpr (KIND == SBH_WINDING) return term_winding(pm, ld_dip(T, S, v), q);
     else return term_affine(pm, q, kp.g);
 }
 
-// child index (0-based) picked by the 24-bit draw x: mass -> number of prefix fractions <= u among
-// all but the last child; count -> the child holding point floor(u * |T|) of the node's range
-__device__ __forceinline__ int pick_child(const TreeView& T, int32_t node, int32_t f, int nc, uint32_t x, int sampling)
+// child index (0-based) picked by the 24-bit draw x: mass -> the number of prefix fractions <= u
+// among all but the last child; count -> the child holding point floor(u * |T|) of the node's
+// range. Both are found by binary search (prefix fractions and child ranges are nondecreasing),
+// which gives the same index as counting.
+__device__ __forceinline__ int pick_child(const TreeView& T, const Stage& S, int32_t node, int32_t f, int nc, uint32_t x,
+                                          int sampling)
 {
-    int pick = 0;
     if (sampling == 0) {
         const float u = unit24(x);
-        for (int k = 0; k < nc - 1; ++k) pick += (__ldg(&T.cdf[f + k]) <= u) ? 1 : 0;
-    } else {
-        const int32_t b = __ldg(&T.nb[node]);
-        const int32_t cnt = __ldg(&T.ne[node]) - b;
-        const int32_t target = b + (int32_t)(((uint64_t)(x >> 8) * (uint64_t)cnt) >> 24);
-        for (int k = 1; k < nc; ++k) pick += (__ldg(&T.nb[f + k]) <= target) ? 1 : 0;
+        int lo = 0, hi = nc - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (ld_cdf(T, S, f + mid) <= u) lo = mid + 1;
+            else hi = mid;
+        }
+        return lo;
     }
-    return pick;
+    const int32_t b = __ldg(&T.nb[node]);
+    const int32_t cnt = __ldg(&T.ne[node]) - b;
+    const int32_t target = b + (int32_t)(((uint64_t)(x >> 8) * (uint64_t)cnt) >> 24);
+    int lo = 1, hi = nc;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(&T.nb[f + mid]) <= target) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo - 1;
 }
 
 struct Params {
@@ -88,7 +141,8 @@ struct Params {
 // One decision per lane (Algorithm 2's loop body up to the break test). On a continue the lane
 // appends a swap task for its node and a decision task for the chosen child.
 template <int KIND>
-__device__ __forceinline__ void decide(const Params& P, WarpState& W, const float* sdiam, bool valid, int32_t node,
+__device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpState& W, const float* sdiam, bool valid,
+                                       int32_t node,
                                        uint32_t tag, int32_t ai, float prr, float dT, float wT, float wa,
                                        uint32_t& d_tail, uint32_t& s_tail)
 {
@@ -101,12 +155,12 @@ __device__ __forceinline__ void decide(const Params& P, WarpState& W, const floa
         const uint32_t depth = (tag >> 5) & 0xFFu, s = tag >> 13;
         const float3 q = make_float3(W.qx[slot], W.qy[slot], W.qz[slot]);
         const uint4 x = philox4x32_10(make_uint4(W.qctr[slot], (uint32_t)ai, s, depth), P.key);
-        const uint32_t mT = __ldg(&T.meta[node]);
-        const int32_t f = __ldg(&T.fc[node]);
+        const uint32_t mT = ld_meta(T, S, node);
+        const int32_t f = ld_fc(T, S, node);
         const int nc = (int)meta_nchild(mT);
-        child = f + pick_child(T, node, f, nc, x.x, P.sampling);
-        const float4 pc = __ldg(&T.pm[child]);
-        const uint32_t mc = __ldg(&T.meta[child]);
+        child = f + pick_child(T, S, node, f, nc, x.x, P.sampling);
+        const float4 pc = ld_pm(T, S, child);
+        const uint32_t mc = ld_meta(T, S, child);
         dc = dist_rn(pc.x, pc.y, pc.z, q);
         float p;
         if (P.rr == 0) p = rr_prob_rn(dT, sdiam[meta_level(mT)], dc, sdiam[meta_level(mc)]);
@@ -147,7 +201,8 @@ __device__ __forceinline__ void decide(const Params& P, WarpState& W, const floa
 
 // Run up to 32 decision tasks from the front of the ring.
 template <int KIND>
-__device__ __forceinline__ void decision_batch(const Params& P, WarpState& W, const float* sdiam, uint32_t& d_head,
+__device__ __forceinline__ void decision_batch(const Params& P, const Stage& S, WarpState& W, const float* sdiam,
+                                               uint32_t& d_head,
                                                uint32_t& d_tail, uint32_t& s_tail)
 {
     const uint32_t avail = d_tail - d_head;
@@ -163,13 +218,14 @@ __device__ __forceinline__ void decision_batch(const Params& P, WarpState& W, co
     }
     __syncwarp();  // every task is read before new ones may reuse its slot
     d_head += take;
-    decide<KIND>(P, W, sdiam, valid, node, tag, ai, prr, dT, wT, wa, d_tail, s_tail);
+    decide<KIND>(P, S, W, sdiam, valid, node, tag, ai, prr, dT, wT, wa, d_tail, s_tail);
 }
 
 // Run up to 32 swap tasks: w * (sum_children m_c f(p_c, q) - m_T f(p_T, q)), added to the
 // query's sum in lane order.
 template <int KIND>
-__device__ __forceinline__ void swap_batch(const Params& P, WarpState& W, uint32_t& s_head, uint32_t s_tail)
+__device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, WarpState& W, uint32_t& s_head,
+                                           uint32_t s_tail)
 {
     const TreeView& T = P.T;
     const uint32_t avail = s_tail - s_head;
@@ -189,24 +245,31 @@ __device__ __forceinline__ void swap_batch(const Params& P, WarpState& W, uint32
     float v = 0.0f, r = 3.0e38f;
     if (valid) {
         const float3 q = make_float3(W.qx[slot], W.qy[slot], W.qz[slot]);
-        const uint32_t m = __ldg(&T.meta[node]);
-        const int32_t f = __ldg(&T.fc[node]);
+        const uint32_t m = ld_meta(T, S, node);
+        const int32_t f = ld_fc(T, S, node);
         const int nc = (int)meta_nchild(m);
-        const float4 pT = __ldg(&T.pm[node]);
+        const float4 pT = ld_pm(T, S, node);
         if constexpr (KIND == SBH_SMOOTHDIST) {
             const float a = P.kp.alpha;
             r = dist_fast(pT, q);
             v = -w * pT.w;
             for (int k = 0; k < nc; ++k) {
-                const float4 pc = __ldg(&T.pm[f + k]);
+                const float4 pc = ld_pm(T, S, f + k);
                 const float d = dist_fast(pc, q);
                 if (d < r) { v *= __expf(-a * (r - d)); r = d; }
                 v = fmaf(w * pc.w, __expf(-a * (d - r)), v);
             }
         } else {
-            float s = 0.0f;
-            for (int k = 0; k < nc; ++k) s += node_value<KIND>(T, f + k, __ldg(&T.pm[f + k]), q, P.kp);
-            v = w * (s - node_value<KIND>(T, node, pT, q, P.kp));
+            // two independent partial sums: two child records in flight per iteration
+            float s0 = 0.0f, s1 = 0.0f;
+            int k = 0;
+            for (; k + 1 < nc; k += 2) {
+                const float4 p0 = ld_pm(T, S, f + k), p1 = ld_pm(T, S, f + k + 1);
+                s0 += node_value<KIND>(T, S, f + k, p0, q, P.kp);
+                s1 += node_value<KIND>(T, S, f + k + 1, p1, q, P.kp);
+            }
+            if (k < nc) s0 += node_value<KIND>(T, S, f + k, ld_pm(T, S, f + k), q, P.kp);
+            v = w * ((s0 + s1) - node_value<KIND>(T, S, node, pT, q, P.kp));
         }
     }
     // lane-ordered sum over the tasks of each query
@@ -240,10 +303,27 @@ __device__ __forceinline__ void swap_batch(const Params& P, WarpState& W, uint32
 }
 
 template <int KIND>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stoch_batched(Params P)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_stoch_batched(Params P, int32_t stage_lo, uint32_t stage_n)
 {
     __shared__ WarpState s_state[kWarpsPerBlock];
     __shared__ float sdiam[kDiamLevels];
+    extern __shared__ float4 s_stage[];
+    Stage S;
+    S.lo = stage_lo;
+    S.n = stage_n;
+    S.pm = s_stage;
+    S.dip = s_stage + stage_n;
+    S.cdf = (float*)(S.dip + (KIND == SBH_WINDING ? stage_n : 0));
+    S.meta = (uint32_t*)(S.cdf + stage_n);
+    S.fc = (int32_t*)(S.meta + stage_n);
+    for (uint32_t i = threadIdx.x; i < stage_n; i += blockDim.x) {
+        const int32_t v = stage_lo + (int32_t)i;
+        S.pm[i] = __ldg(&P.T.pm[v]);
+        if (KIND == SBH_WINDING) S.dip[i] = __ldg(&P.T.dip[v]);
+        S.cdf[i] = __ldg(&P.T.cdf[v]);
+        S.meta[i] = __ldg(&P.T.meta[v]);
+        S.fc[i] = __ldg(&P.T.fc[v]);
+    }
     if (threadIdx.x < kDiamLevels) sdiam[threadIdx.x] = P.T.ctrl->diam[threadIdx.x];
     __syncthreads();
     WarpState& W = s_state[threadIdx.x >> 5];
@@ -272,33 +352,33 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stoch_batched(Params P)
 
         for (int ai = 0; ai < n_sub; ++ai) {
             const int32_t a = first_sub + ai;
-            const float4 pa = __ldg(&T.pm[a]);
-            const uint32_t ma = __ldg(&T.meta[a]);
+            const float4 pa = ld_pm(T, S, a);
+            const uint32_t ma = ld_meta(T, S, a);
             if (active) {  // control variate CV_a
                 if constexpr (KIND == SBH_SMOOTHDIST) {
                     const float d = dist_fast(pa, q);
                     ex.lower(d, P.kp.alpha);
                     ex.acc = fmaf(pa.w, ex.scale(d, P.kp.alpha), ex.acc);
                 } else {
-                    cv += node_value<KIND>(T, a, pa, q, P.kp);
+                    cv += node_value<KIND>(T, S, a, pa, q, P.kp);
                 }
             }
             if (meta_kind(ma) == kPoint) continue;
             const float wa = P.sampling ? (float)(__ldg(&T.ne[a]) - __ldg(&T.nb[a])) : pa.w;
             const float da = dist_rn(pa.x, pa.y, pa.z, q);
             for (int s = 0; s < P.S; ++s) {
-                decide<KIND>(P, W, sdiam, active, a, lane | ((uint32_t)s << 13), ai, 1.0f, da, wa, wa, d_tail, s_tail);
-                while (s_tail - s_head >= 32u) swap_batch<KIND>(P, W, s_head, s_tail);
+                decide<KIND>(P, S, W, sdiam, active, a, lane | ((uint32_t)s << 13), ai, 1.0f, da, wa, wa, d_tail, s_tail);
+                while (s_tail - s_head >= 32u) swap_batch<KIND>(P, S, W, s_head, s_tail);
                 while (d_tail - d_head >= 32u) {
-                    decision_batch<KIND>(P, W, sdiam, d_head, d_tail, s_tail);
-                    while (s_tail - s_head >= 32u) swap_batch<KIND>(P, W, s_head, s_tail);
+                    decision_batch<KIND>(P, S, W, sdiam, d_head, d_tail, s_tail);
+                    while (s_tail - s_head >= 32u) swap_batch<KIND>(P, S, W, s_head, s_tail);
                 }
             }
         }
         // drain the partial batches
         while (d_tail != d_head || s_tail != s_head) {
-            if (s_tail != s_head) swap_batch<KIND>(P, W, s_head, s_tail);
-            if (d_tail != d_head) decision_batch<KIND>(P, W, sdiam, d_head, d_tail, s_tail);
+            if (s_tail != s_head) swap_batch<KIND>(P, S, W, s_head, s_tail);
+            if (d_tail != d_head) decision_batch<KIND>(P, S, W, sdiam, d_head, d_tail, s_tail);
         }
         __syncwarp();
         if (active) {
@@ -318,10 +398,22 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_stoch_batched(Params P)
     }
 }
 
+
+template <int KIND>
+static cudaError_t launch_kind(const Params& P, unsigned blocks, int32_t lo, uint32_t n, cudaStream_t s)
+{
+    const size_t bytes = (size_t)n * (sizeof(float4) * (KIND == SBH_WINDING ? 2 : 1) + 3 * sizeof(uint32_t));
+    cudaError_t e = cudaFuncSetAttribute(k_stoch_batched<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k_stoch_batched<KIND><<<blocks, 32 * kWarpsPerBlock, bytes, s>>>(P, lo, n);
+    return cudaSuccess;
+}
+
 }  // namespace
 
-cudaError_t launch_stoch_batched(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
-                                 uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s)
+cudaError_t launch_stoch_batched(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
+                                 const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
+                                 cudaStream_t s)
 {
     if (nq <= 0) return cudaSuccess;
     Params P;
@@ -331,14 +423,20 @@ cudaError_t launch_stoch_batched(const TreeView& T, const float* Q, int64_t nq, 
     const int64_t tiles = (nq + 31) / 32;
     int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    const unsigned threads = 32 * kWarpsPerBlock;
+    // stage generations 1 and 2 (the subdomains and their children), at most kStageMax nodes
+    const int32_t lo = host_ctrl.max_depth >= 1 ? host_ctrl.depth_base[1] : 0;
+    const int32_t hi = host_ctrl.depth_base[host_ctrl.max_depth >= 2 ? 3 : (host_ctrl.max_depth >= 1 ? 2 : 1)];
+    uint32_t n = (uint32_t)(hi > lo ? hi - lo : 0);
+    if (n > (uint32_t)kStageMax) n = kStageMax;
+    cudaError_t e;
     switch (kp.kind) {
-    case SBH_COULOMB: k_stoch_batched<SBH_COULOMB><<<(unsigned)blocks, threads, 0, s>>>(P); break;
-    case SBH_WINDING: k_stoch_batched<SBH_WINDING><<<(unsigned)blocks, threads, 0, s>>>(P); break;
-    case SBH_SMOOTHDIST: k_stoch_batched<SBH_SMOOTHDIST><<<(unsigned)blocks, threads, 0, s>>>(P); break;
-    case SBH_AFFINE: k_stoch_batched<SBH_AFFINE><<<(unsigned)blocks, threads, 0, s>>>(P); break;
+    case SBH_COULOMB: e = launch_kind<SBH_COULOMB>(P, (unsigned)blocks, lo, n, s); break;
+    case SBH_WINDING: e = launch_kind<SBH_WINDING>(P, (unsigned)blocks, lo, n, s); break;
+    case SBH_SMOOTHDIST: e = launch_kind<SBH_SMOOTHDIST>(P, (unsigned)blocks, lo, n, s); break;
+    case SBH_AFFINE: e = launch_kind<SBH_AFFINE>(P, (unsigned)blocks, lo, n, s); break;
     default: return cudaErrorInvalidValue;
     }
+    if (e != cudaSuccess) return e;
     note_launch();
     return cudaGetLastError();
 }
