@@ -192,13 +192,13 @@ def source_hash(paths):
     return h.hexdigest()[:16]
 
 
-EVAL_SOURCES = ["paper_2506_02219_gb300/csrc/sbh_eval.cu", "paper_2506_02219_gb300/csrc/sbh_internal.cuh"]
+EVAL_SOURCES = ["paper_2506_02219_gb300/csrc/sbh_eval_batched.cu", "paper_2506_02219_gb300/csrc/sbh_internal.cuh"]
 
 
 def profiled_traffic(workload: str):
     """DRAM bytes per query of the estimator kernel from the committed ncu summary, if the kernel
     sources still hash to what was profiled; else None."""
-    path = os.path.join(ROOT, "profiles", f"sbh_stoch_eval_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"k_stoch_batched_{workload}.md")
     if not os.path.exists(path):
         return None
     want = source_hash(EVAL_SOURCES)
@@ -367,7 +367,7 @@ def run_ours(args):
         result["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                               "frac": achieved / peak,
                               "traffic": (traffic_pq * nq) if traffic_pq is not None else None,
-                              "kernel": "k_stoch_eval", "terms_per_query": c[0] / nq,
+                              "kernel": "k_stoch_batched", "terms_per_query": c[0] / nq,
                               "records_per_query": c[1] / nq, "decisions_per_query": c[2] / nq,
                               "flops_per_term": FLOPS_PER_TERM[wl.kernel],
                               "peak_basis": "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
