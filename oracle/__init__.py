@@ -14,6 +14,8 @@ Functions and the passages they follow:
   Tree.replay(...)  Algorithm 2 with Eq. 5 (Russian roulette), Eq. 6 (swap), Eq. 7 (estimator),
                     driven by the same counter-based Philox4x32-10 stream as the GPU kernel.
   Tree.enumerate()  exact mean and variance of Eq. 7 by enumeration (Appendix A).
+  brute_grad, Tree.replay_grad, Tree.enumerate_grad: the same for the query gradient (the
+                    estimator applied to grad_q f with the paths and weights held fixed).
   philox(...)       Philox4x32-10 (Salmon et al., SC'11).
 
 Parity pins (tests/test_oracle_*.py): closed forms for the brute force, hand-built trees,
@@ -82,6 +84,9 @@ def _load():
         lib.sbho_bh.argtypes = [P, C.POINTER(_Kernel), P, i64, C.c_float, P]
         lib.sbho_replay.argtypes = [P, C.POINTER(_Kernel), P, i64, i32, u64, C.POINTER(_Opts), P, P, P, P]
         lib.sbho_enumerate.argtypes = [P, C.POINTER(_Kernel), P, i64, C.POINTER(_Opts), P, P]
+        lib.sbho_brute_grad.argtypes = [C.POINTER(_Kernel), P, P, P, i64, P, i64, P]
+        lib.sbho_replay_grad.argtypes = [P, C.POINTER(_Kernel), P, P, i64, i32, u64, C.POINTER(_Opts), P, P, P, P]
+        lib.sbho_enumerate_grad.argtypes = [P, C.POINTER(_Kernel), P, i64, C.POINTER(_Opts), P]
         lib.sbho_max_threads.restype = i32
         lib.sbho_set_threads.argtypes = [i32]
         _lib = lib
@@ -137,6 +142,18 @@ def brute(points, weights, queries, kind=COULOMB, normals=None, softening=1e-3, 
     out = np.zeros(q.shape[0], dtype=np.float64)
     k = kernel(kind, softening, alpha, affine)
     lib.sbho_brute(C.byref(k), _ptr(pts), _ptr(w), _ptr(nrm), pts.shape[0], _ptr(q), q.shape[0], _ptr(out))
+    return out
+
+
+def brute_grad(points, weights, queries, kind=COULOMB, normals=None, softening=1e-3, alpha=200.0,
+               affine=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Gradient of Eq. 1 with respect to the query position, [nq, 3], FP64 compensated sums."""
+    lib = _load()
+    pts, w, q = _f32(points, 3), _f32(weights), _f32(queries, 3)
+    nrm = _f32(normals, 3)
+    out = np.zeros((q.shape[0], 3), dtype=np.float64)
+    k = kernel(kind, softening, alpha, affine)
+    lib.sbho_brute_grad(C.byref(k), _ptr(pts), _ptr(w), _ptr(nrm), pts.shape[0], _ptr(q), q.shape[0], _ptr(out))
     return out
 
 
@@ -218,6 +235,37 @@ class Tree:
         if return_abs_sum:
             res += (absum,)
         return res if len(res) > 1 else out
+
+    def replay_grad(self, queries, S: int = 1, seed: int = 0, kind=COULOMB, softening=1e-3, alpha=200.0,
+                    affine=(0.0, 0.0, 0.0), sampling=SAMPLE_MASS, rr=RR_PAPER, coherent=False, query_index=None,
+                    eval_at=None):
+        """The estimator with paths and weights drawn at `queries` (FP32 decisions, as replay) and every
+        term replaced by its query gradient evaluated at `eval_at` (default: the same queries, FP64).
+        Returns (value estimate along those paths at eval_at [nq], gradient [nq, 3], sum of |gradient
+        terms| [nq])."""
+        q = _f32(queries, 3)
+        qv = np.ascontiguousarray(q.astype(np.float64) if eval_at is None else np.asarray(eval_at, np.float64)
+                                  .reshape(-1, 3))
+        qidx = None if query_index is None else np.ascontiguousarray(np.asarray(query_index, dtype=np.uint32))
+        val = np.zeros(q.shape[0], np.float64)
+        grad = np.zeros((q.shape[0], 3), np.float64)
+        ab = np.zeros(q.shape[0], np.float64)
+        k = kernel(kind, softening, alpha, affine)
+        o = _opts(sampling, rr, coherent)
+        self._lib.sbho_replay_grad(self._h, C.byref(k), _ptr(q), _ptr(qv), q.shape[0], int(S),
+                                   C.c_uint64(seed & (2**64 - 1)), C.byref(o), _ptr(qidx), _ptr(val), _ptr(grad),
+                                   _ptr(ab))
+        return val, grad, ab
+
+    def enumerate_grad(self, queries, kind=COULOMB, softening=1e-3, alpha=200.0, affine=(0.0, 0.0, 0.0),
+                       sampling=SAMPLE_MASS, rr=RR_PAPER):
+        """Exact mean of the one-sample gradient estimator per query, [nq, 3], by enumeration."""
+        q = _f32(queries, 3)
+        mean = np.zeros((q.shape[0], 3), np.float64)
+        k = kernel(kind, softening, alpha, affine)
+        o = _opts(sampling, rr, False)
+        self._lib.sbho_enumerate_grad(self._h, C.byref(k), _ptr(q), q.shape[0], C.byref(o), _ptr(mean))
+        return mean
 
     def enumerate(self, queries, kind=COULOMB, softening=1e-3, alpha=200.0, affine=(0.0, 0.0, 0.0),
                   sampling=SAMPLE_MASS, rr=RR_PAPER):

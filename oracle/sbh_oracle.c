@@ -121,6 +121,45 @@ static double term(const sbho_kernel *k, const double p[3], double m, const doub
     return 0.0;
 }
 
+/* Gradient with respect to the query q of weight * f(p, q), with d = p - q, r = |d|:
+ *   Coulomb   m d / (r^2 + eps^2)^(3/2)
+ *   winding   (-N / r^3 + 3 (d . N) d / r^5) / (4 pi), 0 at r = 0
+ *   smooth    alpha m exp(-alpha r) d / r, 0 at r = 0
+ *   affine    -m g                                                                              */
+static void term_grad(const sbho_kernel *k, const double p[3], double m, const double dip[3],
+                      const double q[3], double g[3])
+{
+    double d[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+    double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    double c = 0.0;
+    switch (k->kind) {
+    case K_COULOMB: {
+        double e = r2 + k->softening * k->softening;
+        c = m / (e * sqrt(e));
+        for (int a = 0; a < 3; ++a) g[a] = c * d[a];
+        return;
+    }
+    case K_WINDING: {
+        if (r2 == 0.0) { g[0] = g[1] = g[2] = 0.0; return; }
+        double r = sqrt(r2), r3 = r2 * r, r5 = r3 * r2;
+        double dn = d[0] * dip[0] + d[1] * dip[1] + d[2] * dip[2];
+        for (int a = 0; a < 3; ++a) g[a] = (-dip[a] / r3 + 3.0 * dn * d[a] / r5) / (4.0 * M_PI);
+        return;
+    }
+    case K_SMOOTHDIST: {
+        if (r2 == 0.0) { g[0] = g[1] = g[2] = 0.0; return; }
+        double r = sqrt(r2);
+        c = k->alpha * m * exp(-k->alpha * r) / r;
+        for (int a = 0; a < 3; ++a) g[a] = c * d[a];
+        return;
+    }
+    case K_AFFINE:
+        for (int a = 0; a < 3; ++a) g[a] = -m * k->affine[a];
+        return;
+    }
+    g[0] = g[1] = g[2] = 0.0;
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Brute force, Eq. 1: F(q) = sum_i m_i f(p_i, q). Neumaier-compensated FP64 summation.        */
 /* ------------------------------------------------------------------------------------------ */
@@ -153,6 +192,31 @@ SBHO_API void sbho_brute(const sbho_kernel *k, const float *pts, const float *w,
             sum = s;
         }
         out[j] = sum + comp;
+    }
+}
+
+/* grad[3 j + a] = dF/dq_a (q_j) = sum_i d(m_i f(p_i, q))/dq_a, compensated FP64 sums */
+SBHO_API void sbho_brute_grad(const sbho_kernel *k, const float *pts, const float *w, const float *nrm,
+                              int64_t n, const float *queries, int64_t nq, double *grad)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < nq; ++j) {
+        double q[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
+        double sum[3] = {0, 0, 0}, comp[3] = {0, 0, 0};
+        for (int64_t i = 0; i < n; ++i) {
+            double p[3] = {pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]};
+            double m = w[i], dip[3] = {0, 0, 0}, g[3];
+            if (nrm)
+                for (int a = 0; a < 3; ++a) dip[a] = m * (double)nrm[3 * i + a];
+            term_grad(k, p, m, dip, q, g);
+            for (int a = 0; a < 3; ++a) {
+                double t = g[a], s2 = sum[a] + t;
+                if (fabs(sum[a]) >= fabs(t)) comp[a] += (sum[a] - s2) + t;
+                else comp[a] += (t - s2) + sum[a];
+                sum[a] = s2;
+            }
+        }
+        for (int a = 0; a < 3; ++a) grad[3 * j + a] = sum[a] + comp[a];
     }
 }
 
@@ -541,6 +605,24 @@ static double swap_abs(const otree *t, const sbho_kernel *k, int64_t v, const do
     return s + fabs(node_term(t, k, v, q));
 }
 
+static void node_grad(const otree *t, const sbho_kernel *k, int64_t v, const double q[3], double g[3])
+{
+    term_grad(k, &t->com[3 * v], t->mass[v], &t->dip[3 * v], q, g);
+}
+
+/* gradient of the contribution swap (Eq. 6) at node v with respect to q */
+static void swap_grad(const otree *t, const sbho_kernel *k, int64_t v, const double q[3], double g[3])
+{
+    double gc[3];
+    g[0] = g[1] = g[2] = 0.0;
+    for (int c = 0; c < t->nchild[v]; ++c) {
+        node_grad(t, k, t->first_child[v] + c, q, gc);
+        for (int a = 0; a < 3; ++a) g[a] += gc[a];
+    }
+    node_grad(t, k, v, q, gc);
+    for (int a = 0; a < 3; ++a) g[a] -= gc[a];
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Barnes-Hut, Algorithm 1: stop at a leaf or when beta~ >= beta, else recurse into children.   */
 /* The far-field test is taken in FP32 (beta~ as above); sums are FP64.                        */
@@ -634,6 +716,108 @@ SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *quer
         out[j] = F;
         if (nswaps) nswaps[j] = swaps;
         if (abs_sum) abs_sum[j] = A;
+    }
+}
+
+/* The same estimator applied to the kernel's query gradient: the paths, drawn exactly as in     */
+/* sbho_replay (decisions at the FP32 query q_dec), and their weights 1 / (p_agg p_rr) are held  */
+/* fixed, and every term m f is replaced by its gradient at q_val. Because the weights are those */
+/* of a valid sampling of the same tree sums, E[grad] = grad F. With q_val = q_dec this is the    */
+/* adjoint of the estimate; with q_val = q_dec +- h e_a it gives the frozen-path finite           */
+/* difference. val[j] gets the estimate of F at q_val along the same paths, grad[3 j + a] the    */
+/* gradient, abs_grad[j] the sum over terms of |gradient term|_1 (the rounding scale).            */
+SBHO_API void sbho_replay_grad(const void *h, const sbho_kernel *k, const float *q_dec, const double *q_val,
+                               int64_t nq, int32_t S, uint64_t seed, const sbho_opts *opts,
+                               const uint32_t *qidx, double *val, double *grad, double *abs_grad)
+{
+    const otree *t = (const otree *)h;
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    const int sampling = opts ? opts->sampling : SAMPLE_MASS;
+    const int rr = opts ? opts->rr : RR_PAPER;
+    const int coherent = opts ? opts->coherent : 0;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t j = 0; j < nq; ++j) {
+        float q32[3] = {q_dec[3 * j], q_dec[3 * j + 1], q_dec[3 * j + 2]};
+        double q[3] = {q_val[3 * j], q_val[3 * j + 1], q_val[3 * j + 2]};
+        double F = 0, G[3] = {0, 0, 0}, A = 0, g[3];
+        for (int64_t ai = 0; ai < t->n_sub; ++ai) {
+            int64_t a = t->first_sub + ai;
+            F += node_term(t, k, a, q);
+            node_grad(t, k, a, q, g);
+            for (int c = 0; c < 3; ++c) { G[c] += g[c]; A += fabs(g[c]); }
+            for (int32_t s = 0; s < S; ++s) {
+                int64_t T = a;
+                uint32_t depth = 0;
+                double prr = 1.0;
+                while (t->nchild[T] > 0) {
+                    uint32_t ctr[4] = {coherent ? 0u : (qidx ? qidx[j] : (uint32_t)j), (uint32_t)ai, (uint32_t)s, depth};
+                    uint32_t x[4];
+                    sbho_philox4x32_10(ctr, key, x);
+                    int64_t ch = pick_child(t, T, x[0], sampling);
+                    float p = rr_prob32(t, T, ch, q32, rr);
+                    if (unit24f(x[1]) >= p) break;
+                    double pagg = p_in(t, T, a, sampling);
+                    prr *= (double)p;
+                    double wgt = 1.0 / (pagg * prr * (double)S);
+                    F += wgt * swap_delta(t, k, T, q);
+                    swap_grad(t, k, T, q, g);
+                    for (int c = 0; c < 3; ++c) G[c] += wgt * g[c];
+                    for (int cc = 0; cc <= t->nchild[T]; ++cc) {  /* children, then the node itself */
+                        int64_t v = cc < t->nchild[T] ? t->first_child[T] + cc : T;
+                        node_grad(t, k, v, q, g);
+                        for (int c = 0; c < 3; ++c) A += wgt * fabs(g[c]);
+                    }
+                    T = ch;
+                    ++depth;
+                }
+            }
+        }
+        val[j] = F;
+        for (int c = 0; c < 3; ++c) grad[3 * j + c] = G[c];
+        if (abs_grad) abs_grad[j] = A;
+    }
+}
+
+/* Exact mean of the one-sample gradient estimator (S = 1) by enumeration, as sbho_enumerate. */
+static void enum_grad_rec(const otree *t, const sbho_kernel *k, int64_t a, int64_t T, const double q[3],
+                          double P, double prr, int sampling, int rr, double acc[3])
+{
+    if (t->nchild[T] == 0) return;
+    double g[3];
+    swap_grad(t, k, T, q, g);
+    double pagg = p_in(t, T, a, sampling);
+    int64_t fc = t->first_child[T];
+    double tot = 0;
+    for (int c = 0; c < t->nchild[T]; ++c)
+        tot += (sampling == SAMPLE_COUNT) ? (double)(t->end[fc + c] - t->begin[fc + c]) : t->mass[fc + c];
+    for (int c = 0; c < t->nchild[T]; ++c) {
+        int64_t ch = fc + c;
+        double w = (sampling == SAMPLE_COUNT) ? (double)(t->end[ch] - t->begin[ch]) : t->mass[ch];
+        double pi = w / tot;
+        double p = rr_prob64(t, T, ch, q, rr);
+        double prr2 = prr * p;
+        /* this path continues with probability P pi p and then carries the swap term */
+        for (int d = 0; d < 3; ++d) acc[d] += P * pi * p * g[d] / (pagg * prr2);
+        enum_grad_rec(t, k, a, ch, q, P * pi * p, prr2, sampling, rr, acc);
+    }
+}
+
+SBHO_API void sbho_enumerate_grad(const void *h, const sbho_kernel *k, const float *queries, int64_t nq,
+                                  const sbho_opts *opts, double *mean)
+{
+    const otree *t = (const otree *)h;
+    const int sampling = opts ? opts->sampling : SAMPLE_MASS;
+    const int rr = opts ? opts->rr : RR_PAPER;
+    for (int64_t j = 0; j < nq; ++j) {
+        double q[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
+        double E[3] = {0, 0, 0}, g[3];
+        for (int64_t ai = 0; ai < t->n_sub; ++ai) {
+            int64_t a = t->first_sub + ai;
+            node_grad(t, k, a, q, g);
+            for (int d = 0; d < 3; ++d) E[d] += g[d];
+            enum_grad_rec(t, k, a, a, q, 1.0, 1.0, sampling, rr, E);
+        }
+        for (int d = 0; d < 3; ++d) mean[3 * j + d] = E[d];
     }
 }
 

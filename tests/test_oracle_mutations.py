@@ -33,6 +33,11 @@ MUTATIONS = {
         "x->child[0] = make_node(t, b, e, x->level + 1); return x; }"),
     "Philox key schedule": ("if (round > 0) { k0 += weyl0; k1 += weyl1; }",
                             "if (round > 1) { k0 += weyl0; k1 += weyl1; }"),
+    "winding gradient missing its r^-5 term": (
+        "for (int a = 0; a < 3; ++a) g[a] = (-dip[a] / r3 + 3.0 * dn * d[a] / r5) / (4.0 * M_PI);",
+        "for (int a = 0; a < 3; ++a) g[a] = (-dip[a] / r3) / (4.0 * M_PI);"),
+    "Coulomb gradient sign": ("for (int a = 0; a < 3; ++a) g[a] = c * d[a];\n        return;\n    }\n    case K_WINDING",
+                              "for (int a = 0; a < 3; ++a) g[a] = -c * d[a];\n        return;\n    }\n    case K_WINDING"),
 }
 
 
@@ -47,7 +52,7 @@ def test_pins_catch_planted_mistake(tmp_path, name):
     assert src in text, "mutation anchor not found"
     c.write_text(text.replace(src, dst, 1))
     tests = [f"tests/{f}" for f in ("test_oracle_philox.py", "test_oracle_brute.py", "test_oracle_tree.py",
-                                    "test_oracle_estimator.py")]
+                                    "test_oracle_estimator.py", "test_oracle_grad.py")]
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *tests],
                        cwd=tmp_path, capture_output=True, text=True, timeout=900)
     assert r.returncode == 1, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
