@@ -140,6 +140,19 @@ SBH_API sbh_status sbh_eval(const sbh_tree* tree, const float* queries, int64_t 
                     int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
                     float* out, void* stream);
 
+/* Adjoint of sbh_eval with respect to the query positions, under the same random stream: the paths
+ * and their weights 1 / (p(I in T) p(K >= k)) drawn exactly as sbh_eval draws them are held fixed
+ * and every term m f(p, q) of Eq. 7 is replaced by its gradient in q. The weights are a valid
+ * sampling of the same telescoping sums (Eq. 3-4), so E[grad] = grad F exactly; the decisions
+ * themselves (Eq. 5 depends on q) are not differentiated.
+ *   out  device [nq]: the estimate, equal to sbh_eval's up to FP32 summation order
+ *   grad device [nq][3]: d out / d q. For SBH_SMOOTHDIST, d = -log(F)/alpha gives
+ *        grad d = -grad F / (alpha F) (NaN where the estimate of F is <= 0); with opts->raw_sum
+ *        both outputs are the sum F and its gradient. */
+SBH_API sbh_status sbh_eval_grad(const sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel,
+                                 int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
+                                 float* out, float* grad, void* stream);
+
 /* The work sbh_eval does for the same arguments, counted instead of evaluated: the same paths
  * are walked (same decisions) and no output is written. counts: device [4] unsigned 64-bit,
  * accumulated into (the caller zeroes them): [0] kernel terms evaluated (control variates, every

@@ -24,7 +24,7 @@ import numpy as np
 
 __all__ = ["SBHError", "Tree", "EvalOpts", "kernel", "load_library", "sbh_build", "sbh_eval", "sbh_eval_count",
            "sbh_eval_bh", "sbh_eval_brute", "sbh_tree_info", "sbh_tree_export", "sbh_tree_free", "sbh_last_error",
-           "sbh_version", "sbh_kernel_launches", "KERNELS"]
+           "sbh_version", "sbh_kernel_launches", "sbh_eval_grad", "StochasticSum", "KERNELS"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libsbh.so")
@@ -82,14 +82,15 @@ def load_library():
         lib.sbh_eval.argtypes = [P, P, i64, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts), P, P]
         lib.sbh_eval_count.argtypes = [P, P, i64, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts), P, P]
         lib.sbh_kernel_launches.restype = C.c_ulonglong
+        lib.sbh_eval_grad.argtypes = [P, P, i64, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts), P, P, P]
         lib.sbh_eval_bh.argtypes = [P, P, i64, _Kernel, C.c_float, i32, P, P]
         lib.sbh_eval_brute.argtypes = [P, P, P, i64, P, i64, _Kernel, i32, P, P]
         lib.sbh_tree_info.argtypes = [P, i32, C.POINTER(_Meta)]
         lib.sbh_tree_export.argtypes = [P, i32, C.POINTER(_Export)]
         lib.sbh_tree_free.argtypes = [P]
         lib.sbh_tree_free.restype = None
-        for f in ("sbh_build", "sbh_eval", "sbh_eval_count", "sbh_eval_bh", "sbh_eval_brute", "sbh_tree_info",
-                  "sbh_tree_export"):
+        for f in ("sbh_build", "sbh_eval", "sbh_eval_count", "sbh_eval_grad", "sbh_eval_bh", "sbh_eval_brute",
+                  "sbh_tree_info", "sbh_tree_export"):
             getattr(lib, f).restype = i32
         _lib = lib
         return lib
@@ -216,6 +217,58 @@ def sbh_eval_count(tree: Tree, queries, kernel="coulomb", samples_per_subdomain:
                               C.c_void_p(counts.data_ptr()), _stream(stream)))
     c = counts.cpu().tolist()
     return {"terms": c[0], "records": c[1], "decisions": c[2], "cdf_reads": c[3]}
+
+
+def sbh_eval_grad(tree: Tree, queries, kernel="coulomb", samples_per_subdomain: int = 1, seed: int = 0,
+                  opts: EvalOpts | None = None, out=None, grad=None, stream=None, softening: float = 1e-3,
+                  alpha: float = 200.0, affine=(0.0, 0.0, 0.0)):
+    """Estimate and its query gradient under the same random stream; returns (out [nq], grad [nq, 3])."""
+    torch = _torch()
+    lib = load_library()
+    nq = int(queries.shape[0])
+    if out is None:
+        out = torch.empty(nq, dtype=torch.float32, device=queries.device)
+    if grad is None:
+        grad = torch.empty((nq, 3), dtype=torch.float32, device=queries.device)
+    k = _kernel_arg(kernel, softening, alpha, affine)
+    _check(lib.sbh_eval_grad(tree.handle, _dev(queries, "queries", 3), nq, k, int(samples_per_subdomain),
+                             C.c_uint64(int(seed) & (2**64 - 1)), C.byref(opts) if opts is not None else None,
+                             _dev(out, "out"), _dev(grad, "grad", 3), _stream(stream)))
+    return out, grad
+
+
+def _stochastic_sum_function():
+    import torch
+
+    class _StochasticSum(torch.autograd.Function):
+        """out = sbh_eval(tree, queries, ...) with backward d out / d queries from sbh_eval_grad (the adjoint
+        under the same random stream)."""
+
+        @staticmethod
+        def forward(ctx, queries, tree, kernel, samples_per_subdomain, seed, opts, softening, alpha):
+            out, grad = sbh_eval_grad(tree, queries.detach().contiguous(), kernel, samples_per_subdomain, seed, opts,
+                                      softening=softening, alpha=alpha)
+            ctx.save_for_backward(grad)
+            return out
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (grad,) = ctx.saved_tensors
+            return grad_out[:, None] * grad, None, None, None, None, None, None, None
+
+    return _StochasticSum
+
+
+_SS = None
+
+
+def StochasticSum(queries, tree: Tree, kernel="coulomb", samples_per_subdomain: int = 1, seed: int = 0,
+                  opts: EvalOpts | None = None, softening: float = 1e-3, alpha: float = 200.0):
+    """Differentiable estimate: a torch.autograd.Function whose backward is the adjoint traversal."""
+    global _SS
+    if _SS is None:
+        _SS = _stochastic_sum_function()
+    return _SS.apply(queries, tree, kernel, samples_per_subdomain, seed, opts, softening, alpha)
 
 
 def sbh_kernel_launches() -> int:

@@ -207,6 +207,33 @@ sbh_status sbh_eval_count(const sbh_tree* tree, const float* queries, int64_t nq
     return SBH_OK;
 }
 
+sbh_status sbh_eval_grad(const sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel,
+                         int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts, float* out,
+                         float* grad, void* stream)
+{
+    g_err[0] = 0;
+    if (!tree || !tree->t4.built) return fail(SBH_EINVAL, "tree is NULL or not built");
+    if (nq < 0) return fail(SBH_EINVAL, "nq < 0");
+    if (samples_per_subdomain < 1) return fail(SBH_EINVAL, "samples_per_subdomain must be >= 1");
+    sbh::KernelParams kp;
+    sbh_status st = check_kernel(kernel, &kp);
+    if (st != SBH_OK) return st;
+    if (kernel.kind == SBH_WINDING && !tree->has_normals)
+        return fail(SBH_EINVAL, "the winding-number kernel needs a tree built with normals");
+    sbh_eval_opts o = {0, 0, 0, 0};
+    if (opts) o = *opts;
+    if (o.sampling < 0 || o.sampling > 1 || o.rr < 0 || o.rr > 2 || o.seed_mode < 0 || o.seed_mode > 1 ||
+        o.raw_sum < 0 || o.raw_sum > 1)
+        return fail(SBH_EINVAL, "sbh_eval_opts out of range");
+    if (nq == 0) return SBH_OK;
+    if (!device_ptr(queries) || !device_ptr(out) || !device_ptr(grad))
+        return fail(SBH_EINVAL, "queries, out and grad must be device memory");
+    cudaError_t e = sbh::launch_stoch_grad(tree->t4.view(), queries, nq, kp, samples_per_subdomain, seed, o, out, grad,
+                                           (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_eval_grad launch");
+    return SBH_OK;
+}
+
 unsigned long long sbh_kernel_launches(void) { return sbh::g_launches.load(std::memory_order_relaxed); }
 
 sbh_status sbh_eval_bh(sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel, float theta,

@@ -1,5 +1,7 @@
 // sbh_eval.cu -- the stratified path sample estimator (Madan et al. 2025, Sec. 3.3, Eq. 5-7,
-// Algorithm 2) on the 64-ary tree.
+// Algorithm 2) walked one lane per query: the counting variant (sbh_eval_count) and the adjoint
+// (sbh_eval_grad). sbh_eval itself runs the batched schedule of sbh_eval_batched.cu, which
+// evaluates the same terms along the same paths.
 //
 // For each query q and each subdomain a (a child of the root, Sec. 3.3.1):
 //   F += CV_a = m_a f(p_a, q)
@@ -10,14 +12,12 @@
 //       1 / (p(I in T) p(K >= k)), and step into c.
 //   F += (sum of the path terms) / S
 // The random stream is Philox4x32-10 keyed by the seed and counted by (query index, subdomain,
-// sample, depth): word 0 picks the child, word 1 plays the roulette.
+// sample, depth): word 0 picks the child, word 1 plays the roulette. Decisions are taken in FP32
+// with correctly rounded operations in a fixed order; kernel values use fast FP32 arithmetic.
 //
-// Decisions (child pick, roulette) are taken in FP32 with correctly rounded operations in a fixed
-// order; kernel values use fast FP32 arithmetic.
-//
-// This file's kernel walks each query's paths one lane per query; it is the counting variant
-// behind sbh_eval_count (same paths, same decisions). sbh_eval itself runs the batched schedule of
-// sbh_eval_batched.cu, which evaluates the same terms.
+// The adjoint applies the same estimator to grad_q f: paths and weights are those drawn for the
+// value (held fixed), every term m f is replaced by its gradient. The weights are those of a valid
+// sampling of the tree's telescoping sums, so the expectation is exactly grad F.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,61 +25,86 @@
 
 namespace sbh {
 
-template <int KIND>
-struct Terms {
-    // m f(p, q) for node record pm (and its dipole for the winding kernel)
-    static __device__ __forceinline__ float value(const TreeView& T, int32_t v, float4 pm, float3 q,
-                                                  const KernelParams& kp)
+namespace {
+
+constexpr int kModeCount = 0;
+constexpr int kModeGrad = 1;
+
+// Running sum of weighted terms and of their query gradients. The smooth-distance kernel keeps
+// both in units of exp(-alpha ref), ref the smallest distance seen so far.
+template <int KIND, bool GRAD>
+struct Acc {
+    float v = 0.0f;
+    float g[3] = {0.0f, 0.0f, 0.0f};
+    float ref = 3.0e38f;
+
+    // w * m f(p, q) (+ its gradient) for node `node` with record pm
+    __device__ __forceinline__ void add(const TreeView& T, int32_t node, float4 pm, float3 q, const KernelParams& kp,
+                                        float w)
     {
+        const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
         if constexpr (KIND == SBH_COULOMB) {
-            return term_coulomb(pm, q, kp.eps2);
+            const float e = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, kp.eps2)));
+            const float ir = rsqrtf(e);
+            const float t = w * pm.w * ir;
+            v += t;
+            if (GRAD) {
+                const float c = t * ir * ir;  // w m / e^(3/2)
+                g[0] = fmaf(c, dx, g[0]); g[1] = fmaf(c, dy, g[1]); g[2] = fmaf(c, dz, g[2]);
+            }
         } else if constexpr (KIND == SBH_WINDING) {
-            return term_winding(pm, __ldg(&T.dip[v]), q);
-        } else if constexpr (KIND == SBH_AFFINE) {
-            return term_affine(pm, q, kp.g);
+            const float4 N = __ldg(&T.dip[node]);
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (r2 > 0.0f) {
+                const float ir = rsqrtf(r2);
+                const float ir3 = ir * ir * ir;
+                const float dn = fmaf(dx, N.x, fmaf(dy, N.y, dz * N.z));
+                const float s = w * kInv4Pi;
+                v = fmaf(s * dn, ir3, v);
+                if (GRAD) {
+                    const float c = 3.0f * s * dn * ir3 * ir * ir;  // 3 (d.N) / r^5
+                    const float b = -s * ir3;                       // -1 / r^3
+                    g[0] += fmaf(b, N.x, c * dx); g[1] += fmaf(b, N.y, c * dy); g[2] += fmaf(b, N.z, c * dz);
+                }
+            }
+        } else if constexpr (KIND == SBH_SMOOTHDIST) {
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const float ir = rsqrtf(fmaxf(r2, 1e-37f));
+            const float r = r2 * ir;
+            if (r < ref) {
+                const float f = __expf(-kp.alpha * (ref - r));
+                v *= f;
+                if (GRAD) { g[0] *= f; g[1] *= f; g[2] *= f; }
+                ref = r;
+            }
+            const float t = w * pm.w * __expf(-kp.alpha * (r - ref));
+            v += t;
+            if (GRAD && r2 > 0.0f) {
+                const float c = kp.alpha * t * ir;  // alpha w m exp(-alpha r) / r
+                g[0] = fmaf(c, dx, g[0]); g[1] = fmaf(c, dy, g[1]); g[2] = fmaf(c, dz, g[2]);
+            }
         } else {
-            return 0.0f;  // smooth distance goes through the exp accumulator
+            const float t = w * pm.w;
+            v = fmaf(t, 1.0f + fmaf(kp.g[0], dx, fmaf(kp.g[1], dy, kp.g[2] * dz)), v);
+            if (GRAD) { g[0] -= t * kp.g[0]; g[1] -= t * kp.g[1]; g[2] -= t * kp.g[2]; }
         }
     }
 };
 
-// sum_c m_c f(p_c, q) over the children [f, f + nc) of a node, minus m_T f(p_T, q), times w,
-// added to the running accumulator
-// work counters of one thread (compiled out unless COUNT): kernel terms evaluated, node records
-// read by swaps and control variates, decisions (one Philox block each), prefix fractions read
+// work counters of one thread: kernel terms evaluated, node records read by swaps and control
+// variates, decisions (one Philox block each), prefix fractions read
 struct Counters {
     unsigned long long evals = 0, records = 0, decisions = 0, cdf_reads = 0;
 };
 
-template <int KIND>
-__device__ __forceinline__ void add_swap(const TreeView& T, int32_t node, int32_t f, int nc, float4 pT, float dT_fast,
-                                         float3 q, const KernelParams& kp, float w, float& acc, ExpAcc& ex)
-{
-    if constexpr (KIND == SBH_SMOOTHDIST) {
-        for (int k = 0; k < nc; ++k) {
-            const float4 pc = __ldg(&T.pm[f + k]);
-            const float d = dist_fast(pc, q);
-            ex.lower(d, kp.alpha);
-            ex.acc = fmaf(w * pc.w, ex.scale(d, kp.alpha), ex.acc);
-        }
-        ex.lower(dT_fast, kp.alpha);
-        ex.acc = fmaf(-w * pT.w, ex.scale(dT_fast, kp.alpha), ex.acc);
-    } else {
-        float s = 0.0f;
-        for (int k = 0; k < nc; ++k) {
-            const float4 pc = __ldg(&T.pm[f + k]);
-            s += Terms<KIND>::value(T, f + k, pc, q, kp);
-        }
-        acc = fmaf(w, s - Terms<KIND>::value(T, node, pT, q, kp), acc);
-    }
-}
-
-template <int KIND, bool COUNT>
+template <int KIND, int MODE>
 __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __restrict__ Q, int64_t nq,
                                                     KernelParams kp, int S, uint2 key, int sampling, int rr,
                                                     int coherent, int raw_sum, float* __restrict__ out,
-                                                    unsigned long long* __restrict__ counts)
+                                                    float* __restrict__ grad, unsigned long long* __restrict__ counts)
 {
+    constexpr bool COUNT = MODE == kModeCount;
+    constexpr bool GRAD = MODE == kModeGrad;
     Counters cnt;
     __shared__ float sdiam[kDiamLevels];
     if (threadIdx.x < kDiamLevels) sdiam[threadIdx.x] = T.ctrl->diam[threadIdx.x];
@@ -90,23 +115,13 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
 
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nq; j += (int64_t)gridDim.x * blockDim.x) {
         const float3 q = make_float3(Q[3 * j], Q[3 * j + 1], Q[3 * j + 2]);
-        float acc = 0.0f;
-        ExpAcc ex;
-        ex.init(3.0e38f);
+        Acc<KIND, GRAD> acc;
         for (int ai = 0; ai < n_sub; ++ai) {
             const int32_t a = first_sub + ai;
             const float4 pa = __ldg(&T.pm[a]);
             const uint32_t ma = __ldg(&T.meta[a]);
-            // control variate CV_a
-            float ta_fast = 0.0f;
-            if constexpr (KIND == SBH_SMOOTHDIST) {
-                ta_fast = dist_fast(pa, q);
-                ex.lower(ta_fast, kp.alpha);
-                ex.acc = fmaf(pa.w, ex.scale(ta_fast, kp.alpha), ex.acc);
-            } else {
-                acc += Terms<KIND>::value(T, a, pa, q, kp);
-            }
             if (COUNT) { cnt.evals += 1; cnt.records += 1; }
+            else acc.add(T, a, pa, q, kp, 1.0f);  // control variate CV_a
             if (meta_kind(ma) == kPoint) continue;
             // a's weight for p(I in T): aggregate mass or point count
             const float wa = sampling ? (float)(__ldg(&T.ne[a]) - __ldg(&T.nb[a])) : pa.w;
@@ -115,7 +130,7 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                 int32_t node = a;
                 float4 pT = pa;
                 uint32_t mT = ma;
-                float dT = da, dT_fast = ta_fast;
+                float dT = da;
                 float prr = 1.0f;
                 float wT = wa;
                 for (uint32_t depth = 0; meta_kind(mT) != kPoint && depth < (uint32_t)kMaxDepth; ++depth) {
@@ -129,8 +144,8 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                         for (int k = 0; k < nc - 1; ++k) pick += (__ldg(&T.cdf[f + k]) <= u) ? 1 : 0;
                     } else {
                         const int32_t b = __ldg(&T.nb[node]);
-                        const int32_t cnt = __ldg(&T.ne[node]) - b;
-                        const int32_t target = b + (int32_t)(((uint64_t)(x.x >> 8) * (uint64_t)cnt) >> 24);
+                        const int32_t cnt_pts = __ldg(&T.ne[node]) - b;
+                        const int32_t target = b + (int32_t)(((uint64_t)(x.x >> 8) * (uint64_t)cnt_pts) >> 24);
                         for (int k = 1; k < nc; ++k) pick += (__ldg(&T.nb[f + k]) <= target) ? 1 : 0;
                     }
                     if (COUNT) { cnt.decisions += 1; cnt.cdf_reads += (uint64_t)(nc - 1); }
@@ -145,23 +160,39 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                     prr *= p;
                     const float pagg = wT / wa;
                     const float w = 1.0f / (pagg * prr) * invS;
-                    add_swap<KIND>(T, node, f, nc, pT, dT_fast, q, kp, w, acc, ex);
-                    if (COUNT) { cnt.evals += (uint64_t)nc + 1; cnt.records += (uint64_t)nc; }
+                    if (COUNT) {
+                        cnt.evals += (uint64_t)nc + 1;
+                        cnt.records += (uint64_t)nc;
+                    } else {
+                        for (int k = 0; k < nc; ++k) acc.add(T, f + k, __ldg(&T.pm[f + k]), q, kp, w);
+                        acc.add(T, node, pT, q, kp, -w);
+                    }
                     node = c;
                     pT = pc;
                     mT = mc;
                     dT = dc;
-                    if constexpr (KIND == SBH_SMOOTHDIST) dT_fast = dist_fast(pc, q);
                     wT = sampling ? (float)(__ldg(&T.ne[c]) - __ldg(&T.nb[c])) : pc.w;
                 }
             }
         }
         if (COUNT) continue;
         if constexpr (KIND == SBH_SMOOTHDIST) {
-            if (raw_sum) out[j] = ex.acc * __expf(-kp.alpha * ex.ref);
-            else out[j] = ex.acc > 0.0f ? ex.ref - __logf(ex.acc) / kp.alpha : __int_as_float(0x7F800000);
+            // d = ref - log(acc) / alpha; grad d = -grad F / (alpha F): the exp(-alpha ref) units cancel
+            if (raw_sum) {
+                const float sc = __expf(-kp.alpha * acc.ref);
+                out[j] = acc.v * sc;
+                if (GRAD) { grad[3 * j] = acc.g[0] * sc; grad[3 * j + 1] = acc.g[1] * sc; grad[3 * j + 2] = acc.g[2] * sc; }
+            } else {
+                const bool pos = acc.v > 0.0f;
+                out[j] = pos ? acc.ref - __logf(acc.v) / kp.alpha : __int_as_float(0x7F800000);
+                if (GRAD) {
+                    const float c = pos ? -1.0f / (kp.alpha * acc.v) : __int_as_float(0x7FC00000);
+                    grad[3 * j] = c * acc.g[0]; grad[3 * j + 1] = c * acc.g[1]; grad[3 * j + 2] = c * acc.g[2];
+                }
+            }
         } else {
-            out[j] = acc;
+            out[j] = acc.v;
+            if (GRAD) { grad[3 * j] = acc.g[0]; grad[3 * j + 1] = acc.g[1]; grad[3 * j + 2] = acc.g[2]; }
         }
     }
     if (COUNT) {
@@ -174,28 +205,29 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
     }
 }
 
-template <bool COUNT>
-static cudaError_t launch_stoch_impl(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
-                                     uint64_t seed, const sbh_eval_opts& o, float* out,
-                                     unsigned long long* counts, cudaStream_t s)
+template <int MODE>
+cudaError_t launch_lane_impl(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
+                             uint64_t seed, const sbh_eval_opts& o, float* out, float* grad,
+                             unsigned long long* counts, cudaStream_t s)
 {
     if (nq <= 0) return cudaSuccess;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     const int threads = 256;
     int64_t blocks = (nq + threads - 1) / threads;
     if (blocks > 152 * 64) blocks = 152 * 64;
+    const unsigned b = (unsigned)blocks;
     switch (kp.kind) {
     case SBH_COULOMB:
-        k_stoch_eval<SBH_COULOMB, COUNT><<<(unsigned)blocks, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, counts);
+        k_stoch_eval<SBH_COULOMB, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts);
         break;
     case SBH_WINDING:
-        k_stoch_eval<SBH_WINDING, COUNT><<<(unsigned)blocks, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, counts);
+        k_stoch_eval<SBH_WINDING, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts);
         break;
     case SBH_SMOOTHDIST:
-        k_stoch_eval<SBH_SMOOTHDIST, COUNT><<<(unsigned)blocks, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, counts);
+        k_stoch_eval<SBH_SMOOTHDIST, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts);
         break;
     case SBH_AFFINE:
-        k_stoch_eval<SBH_AFFINE, COUNT><<<(unsigned)blocks, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, counts);
+        k_stoch_eval<SBH_AFFINE, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts);
         break;
     default:
         return cudaErrorInvalidValue;
@@ -203,6 +235,8 @@ static cudaError_t launch_stoch_impl(const TreeView& T, const float* Q, int64_t 
     note_launch();
     return cudaGetLastError();
 }
+
+}  // namespace
 
 cudaError_t launch_stoch_eval(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
                               const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
@@ -214,7 +248,13 @@ cudaError_t launch_stoch_eval(const TreeView& T, const TreeCtrl& host_ctrl, cons
 cudaError_t launch_stoch_count(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
                                uint64_t seed, const sbh_eval_opts& o, unsigned long long* counts, cudaStream_t s)
 {
-    return launch_stoch_impl<true>(T, Q, nq, kp, S, seed, o, nullptr, counts, s);
+    return launch_lane_impl<kModeCount>(T, Q, nq, kp, S, seed, o, nullptr, nullptr, counts, s);
+}
+
+cudaError_t launch_stoch_grad(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
+                              uint64_t seed, const sbh_eval_opts& o, float* out, float* grad, cudaStream_t s)
+{
+    return launch_lane_impl<kModeGrad>(T, Q, nq, kp, S, seed, o, out, grad, nullptr, s);
 }
 
 }  // namespace sbh
