@@ -4,8 +4,12 @@
   sides): |g_gpu - g_oracle| <= 1e-4 * A_g on >= 99.9% of queries, A_g the sum of |gradient terms|.
 - Unbiasedness: averaged over seeds, the GPU gradient of the sum lies within 3 sigma of the
   FP64 brute-force gradient of Eq. 1.
-- Smooth distance: the adjoint of d = -log(F)/alpha agrees with central finite differences
-  (h = 1e-4) of the GPU's own d, and at many samples it approaches the FP64 brute-force gradient.
+- Finite differences: with the roulette off (p = 1) and mass-proportional picks no decision and no
+  weight depends on q, so central differences (h = 1e-4) of the GPU's own estimate are the
+  derivative the adjoint computes. (With Eq. 5 the weights 1/p_rr vary smoothly with q; the adjoint
+  holds them fixed, which is what makes it unbiased, and the oracle pins it against frozen-path
+  finite differences.) For the smooth distance, at many samples the adjoint of d = -log(F)/alpha
+  approaches the FP64 brute-force gradient.
 - torch.autograd: StochasticSum's backward is the adjoint.
 """
 import numpy as np
@@ -69,33 +73,40 @@ def test_adjoint_is_unbiased(sbh, oracle_mod, kind):
     assert np.mean(z <= 3.0) >= 0.95 and np.all(z <= 5.0), np.sort(z.ravel())[-6:]
 
 
-def test_smooth_distance_gradient(sbh, oracle_mod):
-    from paper_2506_02219_gb300 import workloads as W
-    pts, w, _ = W.shape_union(30000, 81, n_ellipsoids=6, n_boxes=2)
-    w = np.ones_like(w)
-    rng = np.random.default_rng(3)
-    q = rng.uniform(-1.0, 1.0, (512, 3)).astype(np.float32)
-    t = sbh.sbh_build(dev(pts), dev(w))
-    kw = gpu_kwargs("smoothdist", alpha=200.0)
-    d0, g = sbh.sbh_eval_grad(t, dev(q), seed=9, **kw)
+@pytest.mark.parametrize("kind", ["coulomb", "winding", "smoothdist"])
+def test_adjoint_matches_finite_differences_without_roulette(sbh, oracle_mod, kind):
+    pts, w, nrm, q = _inputs(kind, 20000, 81, 512)
+    t = sbh.sbh_build(dev(pts), dev(w), dev(nrm))
+    kw = gpu_kwargs(kind, alpha=200.0)
+    o = sbh.EvalOpts()
+    o.rr = 1
+    d0, g = sbh.sbh_eval_grad(t, dev(q), seed=9, opts=o, **kw)
     d0, g = d0.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64)
     ok = np.isfinite(d0)
-    # central differences of the GPU's own output (same seed and query index: the same stream)
     h = 1e-4
     fd = np.zeros_like(g)
     for a in range(3):
         e = np.zeros(3, np.float32)
         e[a] = h
-        dp = sbh.sbh_eval(t, dev(q + e), seed=9, **kw).cpu().numpy().astype(np.float64)
-        dm = sbh.sbh_eval(t, dev(q - e), seed=9, **kw).cpu().numpy().astype(np.float64)
+        dp = sbh.sbh_eval(t, dev(q + e), seed=9, opts=o, **kw).cpu().numpy().astype(np.float64)
+        dm = sbh.sbh_eval(t, dev(q - e), seed=9, opts=o, **kw).cpu().numpy().astype(np.float64)
         fd[:, a] = (dp - dm) / (2 * h)
         ok &= np.isfinite(dp) & np.isfinite(dm)
-    rel = np.abs(fd - g).max(1)[ok] / np.maximum(np.abs(g).max(1)[ok], 1e-3)
-    assert np.median(rel) < 5e-3 and np.mean(rel < 5e-2) > 0.9, (np.median(rel), np.mean(rel < 5e-2))
-    # with many samples per subdomain the gradient of the distance approaches the exact one
-    d64, g64 = sbh.sbh_eval_grad(t, dev(q[:128]), samples_per_subdomain=64, seed=1, **kw)
-    F = oracle_mod.brute(pts, w, q[:128], kind=oracle_mod.SMOOTHDIST, alpha=200.0)
-    GF = oracle_mod.brute_grad(pts, w, q[:128], kind=oracle_mod.SMOOTHDIST, alpha=200.0)
+    # FP32 estimates: the difference quotient carries ~1e-7 |F| / h of rounding
+    scale = np.abs(g).max(1) + 1e-3 * np.abs(d0) / h
+    rel = np.abs(fd - g).max(1)[ok] / scale[ok]
+    assert np.median(rel) < 5e-3 and np.mean(rel < 5e-2) > 0.95, (np.median(rel), np.mean(rel < 5e-2))
+
+
+def test_smooth_distance_gradient_approaches_exact(sbh, oracle_mod):
+    from paper_2506_02219_gb300 import workloads as W
+    pts, w, _ = W.shape_union(30000, 81, n_ellipsoids=6, n_boxes=2)
+    w = np.ones_like(w)
+    q = np.random.default_rng(3).uniform(-1.0, 1.0, (128, 3)).astype(np.float32)
+    t = sbh.sbh_build(dev(pts), dev(w))
+    d64, g64 = sbh.sbh_eval_grad(t, dev(q), samples_per_subdomain=64, seed=1, **gpu_kwargs("smoothdist"))
+    F = oracle_mod.brute(pts, w, q, kind=oracle_mod.SMOOTHDIST, alpha=200.0)
+    GF = oracle_mod.brute_grad(pts, w, q, kind=oracle_mod.SMOOTHDIST, alpha=200.0)
     gd = -GF / (200.0 * F[:, None])  # gradient of -log(F)/alpha
     e = np.abs(g64.cpu().numpy() - gd).max(1) / np.abs(gd).max(1)
     assert np.median(e) < 0.05, np.median(e)
