@@ -75,6 +75,9 @@ typedef struct {
     int32_t raw_sum;    /* SBH_SMOOTHDIST only: 1 returns the signed estimate of
                            sum_i m_i exp(-alpha |p_i - q|) itself (FP32; underflows to 0 beyond
                            alpha |p - q| ~ 87) instead of the distance -log(F) / alpha */
+    int32_t schedule;   /* how sbh_eval maps work to threads (same result up to FP32 summation order):
+                           0: a warp runs 32 queries, later path steps run as per-warp task batches;
+                           1: one thread walks each query's paths on its own */
 } sbh_eval_opts;
 
 typedef struct sbh_tree sbh_tree;  /* opaque, library-owned */
@@ -162,6 +165,22 @@ SBH_API sbh_status sbh_eval_grad(const sbh_tree* tree, const float* queries, int
 SBH_API sbh_status sbh_eval_count(const sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel,
                                   int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
                                   unsigned long long* counts, void* stream);
+
+/* Many independent problems in one launch: a plan holds n_sets (tree, queries, output) triples
+ * sharing one kernel, S, seed and options; each launch runs every set in one persistent kernel
+ * whose warps take 32-query tiles from a global counter. Set i's output equals sbh_eval on set i
+ * alone (query indices are local to each set) up to FP32 summation order. Query sets may be empty.
+ *   trees, queries, nq, outs: host arrays of n_sets entries (queries / outs are device buffers)
+ * sbh_multi_plan_create copies the set descriptors to the device and synchronises `stream`; the
+ * buffers must stay valid while the plan is used. sbh_multi_plan_launch enqueues a counter reset
+ * and the kernel on `stream` and allocates nothing. */
+typedef struct sbh_multi_plan sbh_multi_plan;
+SBH_API sbh_status sbh_multi_plan_create(const sbh_tree* const* trees, const float* const* queries,
+                                         const int64_t* nq, float* const* outs, int32_t n_sets, sbh_kernel kernel,
+                                         int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
+                                         void* stream, sbh_multi_plan** plan);
+SBH_API sbh_status sbh_multi_plan_launch(const sbh_multi_plan* plan, void* stream);
+SBH_API void sbh_multi_plan_free(sbh_multi_plan* plan);
 
 /* Deterministic Barnes-Hut (Algorithm 1) on the 8-ary tree: a node is used whole when it is a
  * single point or ||q - p_a|| / |B_a| >= beta = 1 / theta (theta = 0 gives the exact sum).

@@ -24,7 +24,8 @@ import numpy as np
 
 __all__ = ["SBHError", "Tree", "EvalOpts", "kernel", "load_library", "sbh_build", "sbh_eval", "sbh_eval_count",
            "sbh_eval_bh", "sbh_eval_brute", "sbh_tree_info", "sbh_tree_export", "sbh_tree_free", "sbh_last_error",
-           "sbh_version", "sbh_kernel_launches", "sbh_eval_grad", "StochasticSum", "KERNELS"]
+           "sbh_version", "sbh_kernel_launches", "sbh_eval_grad", "StochasticSum", "KERNELS", "eval_opts",
+           "MultiPlan", "sbh_multi_plan_create", "sbh_multi_plan_launch", "sbh_multi_plan_free"]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libsbh.so")
@@ -45,8 +46,16 @@ class _Kernel(C.Structure):
 
 class EvalOpts(C.Structure):
     """sbh_eval_opts: sampling (0 mass, 1 count), rr (0 Eq. 5, 1 off, 2 half), seed_mode (0, 1),
-    raw_sum (smooth distance: 1 returns the estimated sum instead of the distance)."""
-    _fields_ = [("sampling", C.c_int32), ("rr", C.c_int32), ("seed_mode", C.c_int32), ("raw_sum", C.c_int32)]
+    raw_sum (smooth distance: 1 returns the estimated sum instead of the distance), schedule
+    (0: warp task batches, 1: one thread per query)."""
+    _fields_ = [("sampling", C.c_int32), ("rr", C.c_int32), ("seed_mode", C.c_int32), ("raw_sum", C.c_int32),
+                ("schedule", C.c_int32)]
+
+
+def eval_opts(sampling: int = 0, rr: int = 0, seed_mode: int = 0, raw_sum: int = 0, schedule: int = 0) -> EvalOpts:
+    o = EvalOpts()
+    o.sampling, o.rr, o.seed_mode, o.raw_sum, o.schedule = sampling, rr, seed_mode, raw_sum, schedule
+    return o
 
 
 class _Meta(C.Structure):
@@ -83,6 +92,13 @@ def load_library():
         lib.sbh_eval_count.argtypes = [P, P, i64, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts), P, P]
         lib.sbh_kernel_launches.restype = C.c_ulonglong
         lib.sbh_eval_grad.argtypes = [P, P, i64, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts), P, P, P]
+        lib.sbh_multi_plan_create.argtypes = [P, P, P, P, i32, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts), P,
+                                              C.POINTER(P)]
+        lib.sbh_multi_plan_create.restype = i32
+        lib.sbh_multi_plan_launch.argtypes = [P, P]
+        lib.sbh_multi_plan_launch.restype = i32
+        lib.sbh_multi_plan_free.argtypes = [P]
+        lib.sbh_multi_plan_free.restype = None
         lib.sbh_eval_bh.argtypes = [P, P, i64, _Kernel, C.c_float, i32, P, P]
         lib.sbh_eval_brute.argtypes = [P, P, P, i64, P, i64, _Kernel, i32, P, P]
         lib.sbh_tree_info.argtypes = [P, i32, C.POINTER(_Meta)]
@@ -269,6 +285,82 @@ def StochasticSum(queries, tree: Tree, kernel="coulomb", samples_per_subdomain: 
     if _SS is None:
         _SS = _stochastic_sum_function()
     return _SS.apply(queries, tree, kernel, samples_per_subdomain, seed, opts, softening, alpha)
+
+
+class MultiPlan:
+    """Owner of an sbh_multi_plan; keeps the trees, queries and outputs it refers to alive."""
+
+    def __init__(self, handle, trees, queries, outs):
+        self._h = C.c_void_p(handle)
+        self.trees, self.queries, self.outs = list(trees), list(queries), list(outs)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            load_library().sbh_multi_plan_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sbh_multi_plan_create(trees, queries, kernel="coulomb", samples_per_subdomain: int = 1, seed: int = 0,
+                          opts: EvalOpts | None = None, outs=None, stream=None, softening: float = 1e-3,
+                          alpha: float = 200.0, affine=(0.0, 0.0, 0.0)) -> MultiPlan:
+    """A plan that evaluates every (tree, queries) pair in one launch; outputs go to `outs`
+    (allocated here if not given, one [nq] tensor per set)."""
+    torch = _torch()
+    lib = load_library()
+    n = len(trees)
+    if n != len(queries):
+        raise ValueError("one query set per tree")
+    if outs is None:
+        outs = [torch.empty(int(q.shape[0]), dtype=torch.float32, device=q.device) for q in queries]
+    for i, q in enumerate(queries):
+        if q.shape[0] > 0:
+            _dev(q, f"queries[{i}]", 3)
+            _dev(outs[i], f"outs[{i}]")
+    th = (C.c_void_p * n)(*[t.handle.value for t in trees])
+    qh = (C.c_void_p * n)(*[q.data_ptr() if q.shape[0] > 0 else 0 for q in queries])
+    oh = (C.c_void_p * n)(*[o.data_ptr() if o.shape[0] > 0 else 0 for o in outs])
+    nq = (C.c_int64 * n)(*[int(q.shape[0]) for q in queries])
+    k = _kernel_arg(kernel, softening, alpha, affine)
+    h = C.c_void_p()
+    _check(lib.sbh_multi_plan_create(C.cast(th, C.c_void_p), C.cast(qh, C.c_void_p), C.cast(nq, C.c_void_p),
+                                     C.cast(oh, C.c_void_p), n, k, int(samples_per_subdomain),
+                                     C.c_uint64(int(seed) & (2**64 - 1)), C.byref(opts) if opts is not None else None,
+                                     _stream(stream), C.byref(h)))
+    return MultiPlan(h.value, trees, queries, outs)
+
+
+def sbh_multi_plan_launch(plan: MultiPlan, stream=None):
+    """Run every set of the plan in one launch (capturable in a CUDA graph); returns the outputs."""
+    _check(load_library().sbh_multi_plan_launch(plan.handle, _stream(stream)))
+    return plan.outs
+
+
+def sbh_multi_plan_free(plan: MultiPlan) -> None:
+    plan.free()
+
+
+def capture_multi(plan: MultiPlan):
+    """Capture one launch of the plan into a torch.cuda.CUDAGraph; graph.replay() re-runs it."""
+    import torch
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):  # warm-up outside the capture
+        sbh_multi_plan_launch(plan)
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        sbh_multi_plan_launch(plan)
+    return g
 
 
 def sbh_kernel_launches() -> int:

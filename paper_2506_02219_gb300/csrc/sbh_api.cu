@@ -92,6 +92,12 @@ void release(sbh_tree* T, cudaStream_t s)
 
 constexpr int64_t kMaxPoints = (int64_t)1 << 28;
 
+bool opts_ok(const sbh_eval_opts& o)
+{
+    return o.sampling >= 0 && o.sampling <= 1 && o.rr >= 0 && o.rr <= 2 && o.seed_mode >= 0 && o.seed_mode <= 1 &&
+           o.raw_sum >= 0 && o.raw_sum <= 1 && o.schedule >= 0 && o.schedule <= 1;
+}
+
 }  // namespace
 
 extern "C" {
@@ -167,10 +173,9 @@ sbh_status sbh_eval(const sbh_tree* tree, const float* queries, int64_t nq, sbh_
     if (st != SBH_OK) return st;
     if (kernel.kind == SBH_WINDING && !tree->has_normals)
         return fail(SBH_EINVAL, "the winding-number kernel needs a tree built with normals");
-    sbh_eval_opts o = {0, 0, 0, 0};
+    sbh_eval_opts o = {0, 0, 0, 0, 0};
     if (opts) o = *opts;
-    if (o.sampling < 0 || o.sampling > 1 || o.rr < 0 || o.rr > 2 || o.seed_mode < 0 || o.seed_mode > 1 ||
-        o.raw_sum < 0 || o.raw_sum > 1)
+    if (!opts_ok(o))
         return fail(SBH_EINVAL, "sbh_eval_opts out of range");
     if (nq == 0) return SBH_OK;
     if (!device_ptr(queries) || !device_ptr(out)) return fail(SBH_EINVAL, "queries and out must be device memory");
@@ -193,10 +198,9 @@ sbh_status sbh_eval_count(const sbh_tree* tree, const float* queries, int64_t nq
     if (st != SBH_OK) return st;
     if (kernel.kind == SBH_WINDING && !tree->has_normals)
         return fail(SBH_EINVAL, "the winding-number kernel needs a tree built with normals");
-    sbh_eval_opts o = {0, 0, 0, 0};
+    sbh_eval_opts o = {0, 0, 0, 0, 0};
     if (opts) o = *opts;
-    if (o.sampling < 0 || o.sampling > 1 || o.rr < 0 || o.rr > 2 || o.seed_mode < 0 || o.seed_mode > 1 ||
-        o.raw_sum < 0 || o.raw_sum > 1)
+    if (!opts_ok(o))
         return fail(SBH_EINVAL, "sbh_eval_opts out of range");
     if (!device_ptr(counts)) return fail(SBH_EINVAL, "counts must be device memory");
     if (nq == 0) return SBH_OK;
@@ -220,10 +224,9 @@ sbh_status sbh_eval_grad(const sbh_tree* tree, const float* queries, int64_t nq,
     if (st != SBH_OK) return st;
     if (kernel.kind == SBH_WINDING && !tree->has_normals)
         return fail(SBH_EINVAL, "the winding-number kernel needs a tree built with normals");
-    sbh_eval_opts o = {0, 0, 0, 0};
+    sbh_eval_opts o = {0, 0, 0, 0, 0};
     if (opts) o = *opts;
-    if (o.sampling < 0 || o.sampling > 1 || o.rr < 0 || o.rr > 2 || o.seed_mode < 0 || o.seed_mode > 1 ||
-        o.raw_sum < 0 || o.raw_sum > 1)
+    if (!opts_ok(o))
         return fail(SBH_EINVAL, "sbh_eval_opts out of range");
     if (nq == 0) return SBH_OK;
     if (!device_ptr(queries) || !device_ptr(out) || !device_ptr(grad))
@@ -232,6 +235,102 @@ sbh_status sbh_eval_grad(const sbh_tree* tree, const float* queries, int64_t nq,
                                            (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "sbh_eval_grad launch");
     return SBH_OK;
+}
+
+}  // extern "C"
+
+struct sbh_multi_plan {
+    int device = 0;
+    int32_t n_sets = 0;
+    int64_t total_tiles = 0;
+    void* descs = nullptr;                  // device array of set descriptors
+    unsigned long long* counter = nullptr;  // device tile counter
+    sbh::KernelParams kp;
+    int32_t S = 1;
+    uint64_t seed = 0;
+    sbh_eval_opts opts;
+};
+
+extern "C" {
+
+sbh_status sbh_multi_plan_create(const sbh_tree* const* trees, const float* const* queries, const int64_t* nq,
+                                 float* const* outs, int32_t n_sets, sbh_kernel kernel, int32_t samples_per_subdomain,
+                                 uint64_t seed, const sbh_eval_opts* opts, void* stream, sbh_multi_plan** plan)
+{
+    g_err[0] = 0;
+    if (!plan) return fail(SBH_EINVAL, "plan is NULL");
+    *plan = nullptr;
+    if (n_sets < 1 || !trees || !queries || !nq || !outs) return fail(SBH_EINVAL, "n_sets >= 1 and non-NULL arrays");
+    if (samples_per_subdomain < 1) return fail(SBH_EINVAL, "samples_per_subdomain must be >= 1");
+    sbh::KernelParams kp;
+    sbh_status st = check_kernel(kernel, &kp);
+    if (st != SBH_OK) return st;
+    sbh_eval_opts o = {0, 0, 0, 0, 0};
+    if (opts) o = *opts;
+    if (!opts_ok(o)) return fail(SBH_EINVAL, "sbh_eval_opts out of range");
+    const size_t db = sbh::multi_set_desc_bytes();
+    unsigned char* host = new (std::nothrow) unsigned char[db * (size_t)n_sets];
+    if (!host) return fail(SBH_ENOMEM, "host allocation failed");
+    int64_t tiles = 0;
+    for (int32_t i = 0; i < n_sets; ++i) {
+        const sbh_tree* t = trees[i];
+        if (!t || !t->t4.built) { delete[] host; return fail(SBH_EINVAL, "set %d: tree is NULL or not built", i); }
+        if (nq[i] < 0) { delete[] host; return fail(SBH_EINVAL, "set %d: nq < 0", i); }
+        if (kernel.kind == SBH_WINDING && !t->has_normals) {
+            delete[] host;
+            return fail(SBH_EINVAL, "set %d: the winding-number kernel needs a tree built with normals", i);
+        }
+        if (nq[i] > 0 && (!device_ptr(queries[i]) || !device_ptr(outs[i]))) {
+            delete[] host;
+            return fail(SBH_EINVAL, "set %d: queries and out must be device memory", i);
+        }
+        sbh::multi_fill_desc(host + db * (size_t)i, t->t4.view(), queries[i], outs[i], nq[i], tiles);
+        tiles += (nq[i] + 31) / 32;
+    }
+    sbh_multi_plan* P = new (std::nothrow) sbh_multi_plan();
+    if (!P) { delete[] host; return fail(SBH_ENOMEM, "host allocation failed"); }
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaGetDevice(&P->device);
+    cudaError_t e = sbh::dalloc(&P->descs, db * (size_t)n_sets, s);
+    if (e == cudaSuccess) e = sbh::dalloc((void**)&P->counter, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P->descs, host, db * (size_t)n_sets, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    delete[] host;
+    if (e != cudaSuccess) {
+        sbh::dfree(P->descs, s);
+        sbh::dfree(P->counter, s);
+        cudaStreamSynchronize(s);
+        delete P;
+        return cuda_fail(e, "sbh_multi_plan_create");
+    }
+    P->n_sets = n_sets;
+    P->total_tiles = tiles;
+    P->kp = kp;
+    P->S = samples_per_subdomain;
+    P->seed = seed;
+    P->opts = o;
+    *plan = P;
+    return SBH_OK;
+}
+
+sbh_status sbh_multi_plan_launch(const sbh_multi_plan* plan, void* stream)
+{
+    g_err[0] = 0;
+    if (!plan) return fail(SBH_EINVAL, "plan is NULL");
+    cudaError_t e = sbh::launch_stoch_multi(plan->descs, plan->n_sets, plan->total_tiles, plan->counter, plan->kp,
+                                            plan->S, plan->seed, plan->opts, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_multi_plan_launch");
+    return SBH_OK;
+}
+
+void sbh_multi_plan_free(sbh_multi_plan* plan)
+{
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    sbh::dfree(plan->descs, nullptr);
+    sbh::dfree(plan->counter, nullptr);
+    cudaStreamSynchronize(nullptr);
+    delete plan;
 }
 
 unsigned long long sbh_kernel_launches(void) { return sbh::g_launches.load(std::memory_order_relaxed); }

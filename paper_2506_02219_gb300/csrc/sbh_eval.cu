@@ -1,7 +1,8 @@
 // sbh_eval.cu -- the stratified path sample estimator (Madan et al. 2025, Sec. 3.3, Eq. 5-7,
-// Algorithm 2) walked one lane per query: the counting variant (sbh_eval_count) and the adjoint
-// (sbh_eval_grad). sbh_eval itself runs the batched schedule of sbh_eval_batched.cu, which
-// evaluates the same terms along the same paths.
+// Algorithm 2) walked one lane per query: the counting variant (sbh_eval_count), the adjoint
+// (sbh_eval_grad) and sbh_eval's one-lane-per-query schedule (opts->schedule = 1). The default
+// schedule of sbh_eval is the batched one of sbh_eval_batched.cu, which evaluates the same terms
+// along the same paths.
 //
 // For each query q and each subdomain a (a child of the root, Sec. 3.3.1):
 //   F += CV_a = m_a f(p_a, q)
@@ -29,6 +30,7 @@ namespace {
 
 constexpr int kModeCount = 0;
 constexpr int kModeGrad = 1;
+constexpr int kModeEval = 2;
 
 // Running sum of weighted terms and of their query gradients. The smooth-distance kernel keeps
 // both in units of exp(-alpha ref), ref the smallest distance seen so far.
@@ -242,7 +244,14 @@ cudaError_t launch_stoch_eval(const TreeView& T, const TreeCtrl& host_ctrl, cons
                               const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
                               cudaStream_t s)
 {
+    if (o.schedule == 1) return launch_lane_impl<kModeEval>(T, Q, nq, kp, S, seed, o, out, nullptr, nullptr, s);
     return launch_stoch_batched(T, host_ctrl, Q, nq, kp, S, seed, o, out, s);
+}
+
+cudaError_t launch_stoch_lane(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
+                              uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s)
+{
+    return launch_lane_impl<kModeEval>(T, Q, nq, kp, S, seed, o, out, nullptr, nullptr, s);
 }
 
 cudaError_t launch_stoch_count(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,

@@ -17,6 +17,16 @@ cudaError_t launch_stoch_batched(const TreeView& T, const TreeCtrl& host_ctrl, c
                                  const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
                                  cudaStream_t s);
 
+// many sets in one launch: set_descs is a device array of n_sets descriptors filled with
+// multi_fill_desc (host side) and copied to the device; counter is one device word
+cudaError_t launch_stoch_multi(const void* set_descs, int n_sets, int64_t total_tiles, unsigned long long* counter,
+                               const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, cudaStream_t s);
+size_t multi_set_desc_bytes();
+void multi_fill_desc(void* dst, const TreeView& T, const float* Q, float* out, int64_t nq, int64_t tile_begin);
+
+cudaError_t launch_stoch_lane(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
+                              uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s);
+
 cudaError_t launch_stoch_count(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
                                uint64_t seed, const sbh_eval_opts& o, unsigned long long* counts, cudaStream_t s);
 

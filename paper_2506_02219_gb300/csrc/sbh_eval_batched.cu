@@ -302,6 +302,77 @@ __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, Warp
     __syncwarp();
 }
 
+// One tile of 32 queries (query index tile * 32 + lane within the set described by P), run by
+// one warp: control variates and depth-0 decisions lane-parallel, everything else as tasks.
+template <int KIND>
+__device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpState& W, const float* sdiam,
+                                         int64_t tile)
+{
+    const TreeView& T = P.T;
+    const int32_t first_sub = T.ctrl->first_sub;
+    const int n_sub = T.ctrl->n_sub;
+    const uint32_t lane = lane_id();
+    const int64_t j = tile * 32 + lane;
+    const bool active = j < P.nq;
+    float3 q = make_float3(0.f, 0.f, 0.f);
+    if (active) q = make_float3(P.Q[3 * j], P.Q[3 * j + 1], P.Q[3 * j + 2]);
+    W.qx[lane] = q.x; W.qy[lane] = q.y; W.qz[lane] = q.z;
+    W.qctr[lane] = P.coherent ? 0u : (uint32_t)j;
+    W.acc[lane] = 0.0f;
+    W.ref[lane] = 3.0e38f;
+    __syncwarp();
+    float cv = 0.0f;
+    ExpAcc ex;
+    ex.init(3.0e38f);
+    uint32_t d_head = 0, d_tail = 0, s_head = 0, s_tail = 0;
+
+    for (int ai = 0; ai < n_sub; ++ai) {
+        const int32_t a = first_sub + ai;
+        const float4 pa = ld_pm(T, S, a);
+        const uint32_t ma = ld_meta(T, S, a);
+        if (active) {  // control variate CV_a
+            if constexpr (KIND == SBH_SMOOTHDIST) {
+                const float d = dist_fast(pa, q);
+                ex.lower(d, P.kp.alpha);
+                ex.acc = fmaf(pa.w, ex.scale(d, P.kp.alpha), ex.acc);
+            } else {
+                cv += node_value<KIND>(T, S, a, pa, q, P.kp);
+            }
+        }
+        if (meta_kind(ma) == kPoint) continue;
+        const float wa = P.sampling ? (float)(__ldg(&T.ne[a]) - __ldg(&T.nb[a])) : pa.w;
+        const float da = dist_rn(pa.x, pa.y, pa.z, q);
+        for (int s = 0; s < P.S; ++s) {
+            decide<KIND>(P, S, W, sdiam, active, a, lane | ((uint32_t)s << 13), ai, 1.0f, da, wa, wa, d_tail, s_tail);
+            while (s_tail - s_head >= 32u) swap_batch<KIND>(P, S, W, s_head, s_tail);
+            while (d_tail - d_head >= 32u) {
+                decision_batch<KIND>(P, S, W, sdiam, d_head, d_tail, s_tail);
+                while (s_tail - s_head >= 32u) swap_batch<KIND>(P, S, W, s_head, s_tail);
+            }
+        }
+    }
+    // drain the partial batches
+    while (d_tail != d_head || s_tail != s_head) {
+        if (s_tail != s_head) swap_batch<KIND>(P, S, W, s_head, s_tail);
+        if (d_tail != d_head) decision_batch<KIND>(P, S, W, sdiam, d_head, d_tail, s_tail);
+    }
+    __syncwarp();
+    if (active) {
+        if constexpr (KIND == SBH_SMOOTHDIST) {
+            const float a = P.kp.alpha;
+            float r = W.ref[lane], v = W.acc[lane];
+            // merge the swap sum into the control-variate sum
+            if (r < ex.ref) { ex.acc = ex.acc * __expf(-a * (ex.ref - r)) + v; ex.ref = r; }
+            else ex.acc = fmaf(v, __expf(-a * (r - ex.ref)), ex.acc);
+            if (P.raw_sum) P.out[j] = ex.acc * __expf(-a * ex.ref);
+            else P.out[j] = ex.acc > 0.0f ? ex.ref - __logf(ex.acc) / a : __int_as_float(0x7F800000);
+        } else {
+            P.out[j] = cv + W.acc[lane];
+        }
+    }
+    __syncwarp();
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_stoch_batched(Params P, int32_t stage_lo, uint32_t stage_n)
 {
@@ -327,77 +398,69 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_stoch_batched(Params
     if (threadIdx.x < kDiamLevels) sdiam[threadIdx.x] = P.T.ctrl->diam[threadIdx.x];
     __syncthreads();
     WarpState& W = s_state[threadIdx.x >> 5];
-    const TreeView& T = P.T;
-    const int32_t first_sub = T.ctrl->first_sub;
-    const int n_sub = T.ctrl->n_sub;
     const int64_t n_tiles = (P.nq + 31) / 32;
     const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t warp_stride = (int64_t)gridDim.x * kWarpsPerBlock;
-    const uint32_t lane = lane_id();
-
-    for (int64_t tile = warp_global; tile < n_tiles; tile += warp_stride) {
-        const int64_t j = tile * 32 + lane;
-        const bool active = j < P.nq;
-        float3 q = make_float3(0.f, 0.f, 0.f);
-        if (active) q = make_float3(P.Q[3 * j], P.Q[3 * j + 1], P.Q[3 * j + 2]);
-        W.qx[lane] = q.x; W.qy[lane] = q.y; W.qz[lane] = q.z;
-        W.qctr[lane] = P.coherent ? 0u : (uint32_t)j;
-        W.acc[lane] = 0.0f;
-        W.ref[lane] = 3.0e38f;
-        __syncwarp();
-        float cv = 0.0f;
-        ExpAcc ex;
-        ex.init(3.0e38f);
-        uint32_t d_head = 0, d_tail = 0, s_head = 0, s_tail = 0;
-
-        for (int ai = 0; ai < n_sub; ++ai) {
-            const int32_t a = first_sub + ai;
-            const float4 pa = ld_pm(T, S, a);
-            const uint32_t ma = ld_meta(T, S, a);
-            if (active) {  // control variate CV_a
-                if constexpr (KIND == SBH_SMOOTHDIST) {
-                    const float d = dist_fast(pa, q);
-                    ex.lower(d, P.kp.alpha);
-                    ex.acc = fmaf(pa.w, ex.scale(d, P.kp.alpha), ex.acc);
-                } else {
-                    cv += node_value<KIND>(T, S, a, pa, q, P.kp);
-                }
-            }
-            if (meta_kind(ma) == kPoint) continue;
-            const float wa = P.sampling ? (float)(__ldg(&T.ne[a]) - __ldg(&T.nb[a])) : pa.w;
-            const float da = dist_rn(pa.x, pa.y, pa.z, q);
-            for (int s = 0; s < P.S; ++s) {
-                decide<KIND>(P, S, W, sdiam, active, a, lane | ((uint32_t)s << 13), ai, 1.0f, da, wa, wa, d_tail, s_tail);
-                while (s_tail - s_head >= 32u) swap_batch<KIND>(P, S, W, s_head, s_tail);
-                while (d_tail - d_head >= 32u) {
-                    decision_batch<KIND>(P, S, W, sdiam, d_head, d_tail, s_tail);
-                    while (s_tail - s_head >= 32u) swap_batch<KIND>(P, S, W, s_head, s_tail);
-                }
-            }
-        }
-        // drain the partial batches
-        while (d_tail != d_head || s_tail != s_head) {
-            if (s_tail != s_head) swap_batch<KIND>(P, S, W, s_head, s_tail);
-            if (d_tail != d_head) decision_batch<KIND>(P, S, W, sdiam, d_head, d_tail, s_tail);
-        }
-        __syncwarp();
-        if (active) {
-            if constexpr (KIND == SBH_SMOOTHDIST) {
-                const float a = P.kp.alpha;
-                float r = W.ref[lane], v = W.acc[lane];
-                // merge the swap sum into the control-variate sum
-                if (r < ex.ref) { ex.acc = ex.acc * __expf(-a * (ex.ref - r)) + v; ex.ref = r; }
-                else ex.acc = fmaf(v, __expf(-a * (r - ex.ref)), ex.acc);
-                if (P.raw_sum) P.out[j] = ex.acc * __expf(-a * ex.ref);
-                else P.out[j] = ex.acc > 0.0f ? ex.ref - __logf(ex.acc) / a : __int_as_float(0x7F800000);
-            } else {
-                P.out[j] = cv + W.acc[lane];
-            }
-        }
-        __syncwarp();
-    }
+    for (int64_t tile = warp_global; tile < n_tiles; tile += warp_stride) run_tile<KIND>(P, S, W, sdiam, tile);
 }
 
+// ------------------------------------------------------------------------------------------------
+// Many independent problems in one persistent launch: every warp takes the next 32-query tile
+// from a global counter (dynamic balance over sets of very different sizes, no waiting) and runs it
+// against its set's tree. Query indices are local to each set, so every set's output equals what
+// sbh_eval returns for that set alone.
+// ------------------------------------------------------------------------------------------------
+struct SetDesc {
+    TreeView T;
+    const float* Q;
+    float* out;
+    int64_t nq;
+    int64_t tile_begin;  // first global tile of this set
+};
+
+struct MultiParams {
+    const SetDesc* sets;
+    int n_sets;
+    int64_t total_tiles;
+    unsigned long long* counter;
+    Params base;  // kernel, samples, key and options shared by all sets
+};
+
+template <int KIND>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_stoch_multi(MultiParams M)
+{
+    __shared__ WarpState s_state[kWarpsPerBlock];
+    __shared__ float s_diam[kWarpsPerBlock][kDiamLevels];
+    const int warp = threadIdx.x >> 5;
+    WarpState& W = s_state[warp];
+    float* sdiam = s_diam[warp];
+    Stage S;
+    S.lo = 0; S.n = 0; S.pm = nullptr; S.dip = nullptr; S.cdf = nullptr; S.meta = nullptr; S.fc = nullptr;
+    Params P = M.base;
+    int cur = -1;
+    const uint32_t lane = lane_id();
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(M.counter, 1ull);
+        const int64_t tile = (int64_t)__shfl_sync(0xFFFFFFFFu, t, 0);
+        if (tile >= M.total_tiles) break;
+        // the last set whose first tile is <= tile (empty sets are skipped by taking the last)
+        int lo = 0, hi = M.n_sets - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (M.sets[mid].tile_begin <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        if (lo != cur) {
+            cur = lo;
+            const SetDesc& D = M.sets[lo];
+            P.T = D.T; P.Q = D.Q; P.out = D.out; P.nq = D.nq;
+            if (lane < (uint32_t)kDiamLevels) sdiam[lane] = D.T.ctrl->diam[lane];
+            __syncwarp();
+        }
+        run_tile<KIND>(P, S, W, sdiam, tile - M.sets[lo].tile_begin);
+    }
+}
 
 template <int KIND>
 static cudaError_t launch_kind(const Params& P, unsigned blocks, int32_t lo, uint32_t n, cudaStream_t s)
@@ -439,6 +502,46 @@ cudaError_t launch_stoch_batched(const TreeView& T, const TreeCtrl& host_ctrl, c
     if (e != cudaSuccess) return e;
     note_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_stoch_multi(const void* set_descs, int n_sets, int64_t total_tiles, unsigned long long* counter,
+                               const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, cudaStream_t s)
+{
+    if (total_tiles <= 0) return cudaSuccess;
+    MultiParams M;
+    M.sets = (const SetDesc*)set_descs;
+    M.n_sets = n_sets;
+    M.total_tiles = total_tiles;
+    M.counter = counter;
+    Params& P = M.base;
+    P.T = TreeView{}; P.Q = nullptr; P.nq = 0; P.kp = kp; P.S = S; P.out = nullptr;
+    P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    P.sampling = o.sampling; P.rr = o.rr; P.coherent = o.seed_mode; P.raw_sum = o.raw_sum;
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    // persistent: three blocks per SM
+    const unsigned blocks = 152 * 3;
+    switch (kp.kind) {
+    case SBH_COULOMB: k_stoch_multi<SBH_COULOMB><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(M); break;
+    case SBH_WINDING: k_stoch_multi<SBH_WINDING><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(M); break;
+    case SBH_SMOOTHDIST: k_stoch_multi<SBH_SMOOTHDIST><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(M); break;
+    case SBH_AFFINE: k_stoch_multi<SBH_AFFINE><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(M); break;
+    default: return cudaErrorInvalidValue;
+    }
+    note_launch();
+    return cudaGetLastError();
+}
+
+size_t multi_set_desc_bytes() { return sizeof(SetDesc); }
+
+void multi_fill_desc(void* dst, const TreeView& T, const float* Q, float* out, int64_t nq, int64_t tile_begin)
+{
+    SetDesc* d = (SetDesc*)dst;
+    d->T = T;
+    d->Q = Q;
+    d->out = out;
+    d->nq = nq;
+    d->tile_begin = tile_begin;
 }
 
 }  // namespace sbh
