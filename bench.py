@@ -371,6 +371,16 @@ def run_ours(args):
                               "records_per_query": c[1] / nq, "decisions_per_query": c[2] / nq,
                               "flops_per_term": FLOPS_PER_TERM[wl.kernel],
                               "peak_basis": "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
+        # the adjoint (value and query gradient under the same random stream)
+        g_out = torch.empty(nq, dtype=torch.float32, device=dev)
+        g_grad = torch.empty((nq, 3), dtype=torch.float32, device=dev)
+        sbh.sbh_eval_grad(tree, Q, samples_per_subdomain=S, seed=seed, out=g_out, grad=g_grad, **kk)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        sbh.sbh_eval_grad(tree, Q, samples_per_subdomain=S, seed=seed, out=g_out, grad=g_grad, **kk)
+        a1.record(stream)
+        a1.synchronize()
+        result["adjoint"] = {"ms": a0.elapsed_time(a1), "queries_per_s": nq / (a0.elapsed_time(a1) / 1e3)}
         if not args.no_equal_error:
             result["equal_error"] = equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev)
         tree.free()
@@ -417,6 +427,16 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
         o2 = sbh.sbh_eval(tree, Q, samples_per_subdomain=s2, seed=seed, **kk)
         extra[f"S{s2}"] = {"ms": timed(lambda: sbh.sbh_eval(tree, Q, samples_per_subdomain=s2, seed=seed, out=o2, **kk), 2),
                            "median_rel_err": float(np.median(rel_error(wl.kernel, o2[idx].cpu().numpy(), ref)))}
+    # the paper's variants (supplemental: roulette off / fixed 1/2; Algorithm 2's uniform path
+    # index; identical seeding across queries) and the one-thread-per-query schedule, at S = 1
+    variants = {}
+    for name, opt in (("roulette_off", sbh.eval_opts(rr=1)), ("roulette_half", sbh.eval_opts(rr=2)),
+                      ("uniform_path_index", sbh.eval_opts(sampling=1)), ("coherent_seed", sbh.eval_opts(seed_mode=1)),
+                      ("thread_per_query", sbh.eval_opts(schedule=1))):
+        ov = sbh.sbh_eval(tree, Q, samples_per_subdomain=S, seed=seed, opts=opt, **kk)
+        ms = timed(lambda: sbh.sbh_eval(tree, Q, samples_per_subdomain=S, seed=seed, opts=opt, out=ov, **kk), 2)
+        err = float(np.median(rel_error(wl.kernel, ov[idx].cpu().numpy(), ref)))
+        variants[name] = {"ms": ms, "median_rel_err": err}
     bh_out = torch.empty(nq, dtype=torch.float32, device=dev)
     t0 = time.perf_counter()
     sbh.sbh_eval_bh(tree, Q[:1], theta=0.5, **kk)  # builds the 8-ary tree
@@ -429,13 +449,21 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
             e = sbh.sbh_eval_bh(tree, Qs, theta=theta, warp_vote=vote, **kk).cpu().numpy()
             sweep.append({"theta": theta, "warp_vote": vote, "ms": ms,
                           "median_rel_err": float(np.median(rel_error(wl.kernel, e, ref)))})
-    best = None
-    for vote in (True, False):
-        pts = [(s["median_rel_err"], s["ms"]) for s in sweep if s["warp_vote"] == vote and s["median_rel_err"] > 0]
-        t_bh, extrap = interp_loglog(err_s, [p[0] for p in pts], [p[1] for p in pts])
-        if best is None or t_bh < best[0]:
-            best = (t_bh, extrap, vote)
-    return {"stochastic": {"S": S, "ms": eval_ms, "median_rel_err": err_s, **extra},
+    def bh_time_at(err):
+        best = None
+        for vote in (True, False):
+            pts = [(s["median_rel_err"], s["ms"]) for s in sweep if s["warp_vote"] == vote and s["median_rel_err"] > 0]
+            t_bh, extrap = interp_loglog(err, [p[0] for p in pts], [p[1] for p in pts])
+            if best is None or t_bh < best[0]:
+                best = (t_bh, extrap, vote)
+        return best
+
+    best = bh_time_at(err_s)
+    for v in list(extra.values()) + list(variants.values()):
+        t_bh, extrap, _ = bh_time_at(v["median_rel_err"])
+        v["bh_ms_at_equal_error"] = t_bh
+        v["speedup_vs_bh"] = t_bh / v["ms"]
+    return {"stochastic": {"S": S, "ms": eval_ms, "median_rel_err": err_s, **extra}, "variants": variants,
             "bh_sweep": sweep, "bh_tree_build_ms": bh_build_ms,
             "bh_ms_at_equal_error": best[0], "bh_warp_vote": best[2], "extrapolated": best[1],
             "speedup_vs_bh_at_equal_median_error": best[0] / eval_ms,
@@ -476,13 +504,81 @@ def run_reference(args):
                               "d2h_bytes_per_step": 0}}), flush=True)
 
 
+def batched_sets(rank: int = 0, n_sets: int = 64):
+    """64 independent problems: sources log-uniform in [2^10, 2^20] (shape unions with area weights),
+    queries log-uniform in [2^8, 2^18] uniform in each set's bounding box."""
+    from paper_2506_02219_gb300 import workloads as W
+    rng = np.random.default_rng(W.BASE_SEED + 3 + 1000 * rank)
+    sets = []
+    for i in range(n_sets):
+        n = int(2 ** rng.uniform(10, 20))
+        nq = int(2 ** rng.uniform(8, 18))
+        p, w, _ = W.shape_union(n, int(rng.integers(1 << 30)), n_ellipsoids=4, n_boxes=2)
+        lo, hi = p.min(0), p.max(0)
+        q = (lo + rng.random((nq, 3)) * (hi - lo)).astype(np.float32)
+        sets.append((p, w, q))
+    return sets
+
+
+def run_batched(args):
+    """Many independent source/query sets in one persistent, graph-captured launch; S and leaf size
+    from the autotuner (largest set, target = the median error of S = 1, leaf 1). A step is one replay
+    of the captured launch (the trees are built once, their build time is reported)."""
+    import torch
+    import paper_2506_02219_gb300 as sbh
+    from paper_2506_02219_gb300 import _build, autotune
+    _build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    sets = batched_sets()
+    big = max(range(len(sets)), key=lambda i: sets[i][0].shape[0])
+    p, w, q = sets[big]
+    tune = autotune.autotune(torch.from_numpy(p).to(dev), torch.from_numpy(w).to(dev), torch.from_numpy(q).to(dev),
+                             "coulomb", leaf_sizes=(1, 2, 4), samples=(1, 2), schedules=(0,))
+    leaf, S = tune["best"]["leaf_size"], tune["best"]["S"]
+    t0 = time.perf_counter()
+    trees, Qs = [], []
+    for p, w, q in sets:
+        trees.append(sbh.sbh_build(torch.from_numpy(p).to(dev), torch.from_numpy(w).to(dev), leaf_size=leaf))
+        Qs.append(torch.from_numpy(q).to(dev))
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t0
+    plan = sbh.sbh_multi_plan_create(trees, Qs, "coulomb", S, seed=0x5BA7)
+    graph = sbh.capture_multi(plan)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = sbh.sbh_kernel_launches()
+    e0.record()
+    for _ in range(args.steps):
+        graph.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    total_q = sum(int(q.shape[0]) for q in Qs)
+    print(json.dumps({"metric": METRIC, "value": total_q / (ms / 1e3), "unit": "queries/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": "batched_64sets_coulomb", "sets": len(sets),
+                                 "sources": int(sum(s[0].shape[0] for s in sets)), "queries": total_q,
+                                 "samples_per_subdomain": S, "leaf_size": leaf,
+                                 "step": "one replay of the graph-captured multi-set launch"},
+                      "build_s_all_sets": build_s, "autotune": tune, "clocks": clk,
+                      "gpu_launches": sbh.sbh_kernel_launches() - launches0}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="winding", choices=["winding", "cube", "slice_coulomb", "slice_smoothdist"])
+    ap.add_argument("--workload", default="winding",
+                    choices=["winding", "cube", "slice_coulomb", "slice_smoothdist", "batched"])
     ap.add_argument("--S", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-equal-error", action="store_true")
@@ -492,6 +588,8 @@ def main(argv=None):
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 
