@@ -87,6 +87,12 @@ def _load():
         lib.sbho_brute_grad.argtypes = [C.POINTER(_Kernel), P, P, P, i64, P, i64, P]
         lib.sbho_replay_grad.argtypes = [P, C.POINTER(_Kernel), P, P, i64, i32, u64, C.POINTER(_Opts), P, P, P, P]
         lib.sbho_enumerate_grad.argtypes = [P, C.POINTER(_Kernel), P, i64, C.POINTER(_Opts), P]
+        lib.sbho_mlp_nparam.restype = i32
+        lib.sbho_mlp_forward.argtypes = [P, P, i64, P]
+        lib.sbho_mlp_loss_grad.argtypes = [P, P, P, P, i64, P]
+        lib.sbho_mlp_loss_grad.restype = C.c_double
+        lib.sbho_child_features.argtypes = [P, i64, P, i32, P]
+        lib.sbho_enumerate_learned.argtypes = [P, C.POINTER(_Kernel), P, C.c_double, P, i64, P, P]
         lib.sbho_max_threads.restype = i32
         lib.sbho_set_threads.argtypes = [i32]
         _lib = lib
@@ -267,6 +273,27 @@ class Tree:
         self._lib.sbho_enumerate_grad(self._h, C.byref(k), _ptr(q), q.shape[0], C.byref(o), _ptr(mean))
         return mean
 
+    def child_features(self, node: int, query, use_dipole: bool = False) -> np.ndarray:
+        """Learned-proposal features [nchild, 6] of the children of `node` at `query` (FP64)."""
+        e = self.export()
+        nc = int(e["nchild"][node])
+        x = np.zeros((nc, 6), np.float64)
+        q = _f32(np.asarray(query).reshape(1, 3), 3)
+        self._lib.sbho_child_features(self._h, int(node), _ptr(q), int(bool(use_dipole)), _ptr(x))
+        return x
+
+    def enumerate_learned(self, queries, weights, eps: float = 0.1, kind=COULOMB, softening=1e-3, alpha=200.0,
+                          affine=(0.0, 0.0, 0.0)):
+        """Exact (mean, variance) of the one-sample estimator with the learned proposal."""
+        q = _f32(queries, 3)
+        w = np.ascontiguousarray(np.asarray(weights, np.float64))
+        mean = np.zeros(q.shape[0], np.float64)
+        var = np.zeros(q.shape[0], np.float64)
+        k = kernel(kind, softening, alpha, affine)
+        self._lib.sbho_enumerate_learned(self._h, C.byref(k), _ptr(w), C.c_double(eps), _ptr(q), q.shape[0],
+                                         _ptr(mean), _ptr(var))
+        return mean, var
+
     def enumerate(self, queries, kind=COULOMB, softening=1e-3, alpha=200.0, affine=(0.0, 0.0, 0.0),
                   sampling=SAMPLE_MASS, rr=RR_PAPER):
         """Exact (mean, variance) of the one-sample estimator per query, by enumeration."""
@@ -277,6 +304,32 @@ class Tree:
         o = _opts(sampling, rr, False)
         self._lib.sbho_enumerate(self._h, C.byref(k), _ptr(q), q.shape[0], C.byref(o), _ptr(mean), _ptr(var))
         return mean, var
+
+
+MLP_NPARAM = 1313  # W1[32][6], b1[32], W2[32][32], b2[32], w3[32], b3
+
+
+def mlp_forward(weights, feats) -> np.ndarray:
+    """Scores of the learned proposal's 6-32-32-1 ReLU network (FP64) for feature rows [n, 6]."""
+    lib = _load()
+    w = np.ascontiguousarray(np.asarray(weights, np.float64))
+    x = np.ascontiguousarray(np.asarray(feats, np.float64).reshape(-1, 6))
+    out = np.zeros(x.shape[0], np.float64)
+    lib.sbho_mlp_forward(_ptr(w), _ptr(x), x.shape[0], _ptr(out))
+    return out
+
+
+def mlp_loss_grad(weights, feats, targets, offsets):
+    """Mean over decision sets of the cross-entropy between softmax(scores) and the normalised
+    targets of each set (rows offsets[s]..offsets[s+1]-1), and its gradient (FP64)."""
+    lib = _load()
+    w = np.ascontiguousarray(np.asarray(weights, np.float64))
+    x = np.ascontiguousarray(np.asarray(feats, np.float64).reshape(-1, 6))
+    t = np.ascontiguousarray(np.asarray(targets, np.float64))
+    off = np.ascontiguousarray(np.asarray(offsets, np.int64))
+    g = np.zeros(MLP_NPARAM, np.float64)
+    loss = lib.sbho_mlp_loss_grad(_ptr(w), _ptr(x), _ptr(t), _ptr(off), off.shape[0] - 1, _ptr(g))
+    return float(loss), g
 
 
 def max_threads() -> int:

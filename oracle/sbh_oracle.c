@@ -822,13 +822,200 @@ SBHO_API void sbho_enumerate_grad(const void *h, const sbho_kernel *k, const flo
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Learned child proposal (a project extension; the paper samples the path index uniformly and  */
+/* names importance sampling as future work, Sec. 3.3). A 6-32-32-1 ReLU network scores each    */
+/* child c of a node T from query-relative features; the proposal mixes its softmax with the    */
+/* mass-proportional one: pi_c = (1 - eps) softmax(s)_c + eps m_c / m_T, every pi_c > 0, so the  */
+/* estimator stays unbiased with p_agg the product of the pi's along the path.                   */
+/* Parameter layout (1313 values): W1[32][6], b1[32], W2[32][32], b2[32], w3[32], b3.           */
+/* ------------------------------------------------------------------------------------------ */
+typedef struct { double e1, e2; } moments;  /* sums of P V and P V^2 over outcomes */
+
+enum { MLP_IN = 6, MLP_H = 32, MLP_NPARAM = MLP_H * MLP_IN + MLP_H + MLP_H * MLP_H + MLP_H + MLP_H + 1 };
+
+/* features of child c of node T at query q:
+ *   ln(d_c / |B_c|), ln(m_c / m_T), ln(|B_c| / |B_T|), ln(d_c / d_T),
+ *   |N_c| / m_c and cos(p_c - q, N_c) (dipole kernel only, else 0); distances guarded by 1e-6 |B| */
+static void child_features(const otree *t, int64_t T, int64_t c, const double q[3], int use_dipole, double x[6])
+{
+    double dT = 0, dc = 0, v[3];
+    for (int a = 0; a < 3; ++a) {
+        double y = t->com[3 * T + a] - q[a];
+        v[a] = t->com[3 * c + a] - q[a];
+        dT += y * y;
+        dc += v[a] * v[a];
+    }
+    double BT = ldexp(sqrt(3.0) * t->side, -(t->bits / 3) * t->level[T]);
+    double Bc = ldexp(sqrt(3.0) * t->side, -(t->bits / 3) * t->level[c]);
+    dT = sqrt(dT) + 1e-6 * BT;
+    dc = sqrt(dc) + 1e-6 * Bc;
+    x[0] = log(dc / Bc);
+    x[1] = log(t->mass[c] / t->mass[T]);
+    x[2] = log(Bc / BT);
+    x[3] = log(dc / dT);
+    x[4] = 0.0;
+    x[5] = 0.0;
+    if (use_dipole) {
+        const double *N = &t->dip[3 * c];
+        double nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+        x[4] = nn / t->mass[c];
+        x[5] = nn > 0 ? (v[0] * N[0] + v[1] * N[1] + v[2] * N[2]) / (dc * nn) : 0.0;
+    }
+}
+
+/* score of one feature row; h1, h2 (optional) receive the hidden activations */
+static double mlp_score(const double *w, const double x[6], double *h1o, double *h2o)
+{
+    const double *W1 = w, *b1 = W1 + MLP_H * MLP_IN, *W2 = b1 + MLP_H, *b2 = W2 + MLP_H * MLP_H,
+                 *w3 = b2 + MLP_H, *b3 = w3 + MLP_H;
+    double h1[MLP_H], h2[MLP_H];
+    for (int i = 0; i < MLP_H; ++i) {
+        double z = b1[i];
+        for (int k = 0; k < MLP_IN; ++k) z += W1[i * MLP_IN + k] * x[k];
+        h1[i] = z > 0 ? z : 0;
+    }
+    double s = b3[0];
+    for (int i = 0; i < MLP_H; ++i) {
+        double z = b2[i];
+        for (int k = 0; k < MLP_H; ++k) z += W2[i * MLP_H + k] * h1[k];
+        h2[i] = z > 0 ? z : 0;
+        s += w3[i] * h2[i];
+    }
+    if (h1o) memcpy(h1o, h1, sizeof(h1));
+    if (h2o) memcpy(h2o, h2, sizeof(h2));
+    return s;
+}
+
+SBHO_API int32_t sbho_mlp_nparam(void) { return MLP_NPARAM; }
+
+SBHO_API void sbho_mlp_forward(const double *w, const double *feats, int64_t n, double *scores)
+{
+    for (int64_t r = 0; r < n; ++r) scores[r] = mlp_score(w, &feats[6 * r], NULL, NULL);
+}
+
+/* Loss over decision sets (rows off[s] .. off[s+1]-1): mean over sets of the cross-entropy
+ * -sum_c t_c log softmax(s)_c with targets t normalised per set; grad (MLP_NPARAM) of the loss. */
+SBHO_API double sbho_mlp_loss_grad(const double *w, const double *feats, const double *targets, const int64_t *off,
+                                   int64_t n_sets, double *grad)
+{
+    memset(grad, 0, sizeof(double) * MLP_NPARAM);
+    double *gW1 = grad, *gb1 = gW1 + MLP_H * MLP_IN, *gW2 = gb1 + MLP_H, *gb2 = gW2 + MLP_H * MLP_H,
+           *gw3 = gb2 + MLP_H, *gb3 = gw3 + MLP_H;
+    const double *W2 = w + MLP_H * MLP_IN + MLP_H, *w3 = W2 + MLP_H * MLP_H + MLP_H;
+    double loss = 0;
+    for (int64_t st = 0; st < n_sets; ++st) {
+        int64_t r0 = off[st], r1 = off[st + 1];
+        int64_t nc = r1 - r0;
+        double *sc = (double *)malloc(sizeof(double) * (size_t)nc);
+        double mx = -1e300, tsum = 0;
+        for (int64_t r = r0; r < r1; ++r) {
+            sc[r - r0] = mlp_score(w, &feats[6 * r], NULL, NULL);
+            if (sc[r - r0] > mx) mx = sc[r - r0];
+            tsum += targets[r];
+        }
+        double z = 0;
+        for (int64_t i = 0; i < nc; ++i) z += exp(sc[i] - mx);
+        for (int64_t r = r0; r < r1; ++r) {
+            double pr = exp(sc[r - r0] - mx) / z;
+            double tr = targets[r] / tsum;
+            loss -= tr * (sc[r - r0] - mx - log(z)) / (double)n_sets;
+            double ds = (pr - tr) / (double)n_sets;  /* d loss / d score */
+            double h1[MLP_H], h2[MLP_H], dh2[MLP_H], dh1[MLP_H];
+            mlp_score(w, &feats[6 * r], h1, h2);
+            gb3[0] += ds;
+            for (int i = 0; i < MLP_H; ++i) {
+                gw3[i] += ds * h2[i];
+                dh2[i] = h2[i] > 0 ? ds * w3[i] : 0.0;
+                gb2[i] += dh2[i];
+            }
+            for (int k = 0; k < MLP_H; ++k) {
+                double acc = 0;
+                for (int i = 0; i < MLP_H; ++i) {
+                    gW2[i * MLP_H + k] += dh2[i] * h1[k];
+                    acc += W2[i * MLP_H + k] * dh2[i];
+                }
+                dh1[k] = h1[k] > 0 ? acc : 0.0;
+                gb1[k] += dh1[k];
+                for (int m = 0; m < MLP_IN; ++m) gW1[k * MLP_IN + m] += dh1[k] * feats[6 * r + m];
+            }
+        }
+        free(sc);
+    }
+    return loss;
+}
+
+/* proposal probabilities of the children of T: (1 - eps) softmax(scores) + eps m_c / m_T */
+static void learned_probs(const otree *t, const double *w, double eps, int use_dipole, int64_t T, const double q[3],
+                          double *pi)
+{
+    int nc = t->nchild[T];
+    int64_t fc = t->first_child[T];
+    double mx = -1e300, z = 0, mt = 0, x[6];
+    for (int c = 0; c < nc; ++c) {
+        child_features(t, T, fc + c, q, use_dipole, x);
+        pi[c] = mlp_score(w, x, NULL, NULL);
+        if (pi[c] > mx) mx = pi[c];
+        mt += t->mass[fc + c];
+    }
+    for (int c = 0; c < nc; ++c) { pi[c] = exp(pi[c] - mx); z += pi[c]; }
+    for (int c = 0; c < nc; ++c) pi[c] = (1.0 - eps) * pi[c] / z + eps * t->mass[fc + c] / mt;
+}
+
+/* features of every child of T at q, rows written to x (6 per child) */
+SBHO_API void sbho_child_features(const void *h, int64_t T, const float *q32, int32_t use_dipole, double *x)
+{
+    const otree *t = (const otree *)h;
+    double q[3] = {q32[0], q32[1], q32[2]};
+    for (int c = 0; c < t->nchild[T]; ++c) child_features(t, T, t->first_child[T] + c, q, use_dipole, &x[6 * c]);
+}
+
+/* exact mean and variance of the one-sample estimator with the learned proposal */
+static void enum_learned_rec(const otree *t, const sbho_kernel *k, const double *w, double eps, int64_t T,
+                             const double q[3], double P, double V, double ppath, double prr, moments *acc)
+{
+    if (t->nchild[T] == 0) { acc->e1 += P * V; acc->e2 += P * V * V; return; }
+    double delta = swap_delta(t, k, T, q);
+    int nc = t->nchild[T];
+    double *pi = (double *)malloc(sizeof(double) * (size_t)nc);
+    learned_probs(t, w, eps, k->kind == K_WINDING, T, q, pi);
+    for (int c = 0; c < nc; ++c) {
+        int64_t ch = t->first_child[T] + c;
+        double p = rr_prob64(t, T, ch, q, RR_PAPER);
+        double Pstop = P * pi[c] * (1.0 - p);
+        acc->e1 += Pstop * V;
+        acc->e2 += Pstop * V * V;
+        double prr2 = prr * p;
+        enum_learned_rec(t, k, w, eps, ch, q, P * pi[c] * p, V + delta / (ppath * prr2), ppath * pi[c], prr2, acc);
+    }
+    free(pi);
+}
+
+SBHO_API void sbho_enumerate_learned(const void *h, const sbho_kernel *k, const double *w, double eps,
+                                     const float *queries, int64_t nq, double *mean, double *var)
+{
+    const otree *t = (const otree *)h;
+    for (int64_t j = 0; j < nq; ++j) {
+        double q[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
+        double E = 0, Var = 0;
+        for (int64_t ai = 0; ai < t->n_sub; ++ai) {
+            int64_t a = t->first_sub + ai;
+            moments m = {0, 0};
+            enum_learned_rec(t, k, w, eps, a, q, 1.0, 0.0, 1.0, 1.0, &m);
+            E += node_term(t, k, a, q) + m.e1;
+            Var += m.e2 - m.e1 * m.e1;
+        }
+        mean[j] = E;
+        var[j] = Var;
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Exact mean and variance of the one-sample estimator (S = 1) by enumerating every outcome    */
 /* of the sampler: at node T reached with probability P and running estimate V, each child c   */
 /* is taken with probability pi_c and continued with probability p (Eq. 5); stopping ends the  */
 /* path with value V, continuing adds Delta_T / (p_agg p_rr). This is the sum the proof of the */
 /* theorem (Appendix A) rearranges. Subdomains are independent, so variances add.             */
 /* ------------------------------------------------------------------------------------------ */
-typedef struct { double e1, e2; } moments;
 
 static void enum_rec(const otree *t, const sbho_kernel *k, int64_t a, int64_t T, const double q[3],
                      double P, double V, double prr, int sampling, int rr, moments *acc)

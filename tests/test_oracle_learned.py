@@ -1,0 +1,67 @@
+"""Pins of the oracle's learned child proposal (a project extension of Sec. 3.3's path sampling).
+
+- The network's loss gradient against central finite differences (FP64).
+- A hand-built network with a closed-form score.
+- Unbiasedness with any proposal that keeps every child probability > 0: the enumerated mean of the
+  estimator with the learned proposal equals the brute-force sum to 1e-12, for random weights.
+- The features are invariant to translating and scaling the whole problem.
+"""
+import numpy as np
+import pytest
+
+from test_oracle_estimator import KINDS, _setup
+
+
+def test_loss_gradient_matches_finite_differences(oracle_mod):
+    rng = np.random.default_rng(0)
+    w = rng.normal(scale=0.3, size=oracle_mod.MLP_NPARAM)
+    sizes = [2, 5, 17, 64]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    x = rng.normal(size=(off[-1], 6))
+    t = rng.random(off[-1])
+    loss, g = oracle_mod.mlp_loss_grad(w, x, t, off)
+    idx = rng.choice(oracle_mod.MLP_NPARAM, 60, replace=False)
+    idx = np.unique(np.concatenate([idx, [0, 191, 192, 223, 224, 1247, 1248, 1279, 1280, 1311, 1312]]))
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(w)
+        e[i] = h
+        fd = (oracle_mod.mlp_loss_grad(w + e, x, t, off)[0] - oracle_mod.mlp_loss_grad(w - e, x, t, off)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g).max()), (i, fd, g[i])
+
+
+def test_hand_built_network(oracle_mod):
+    w = np.zeros(oracle_mod.MLP_NPARAM)
+    # W1 row 0 = e_0 (score path through hidden unit 0 of both layers), W2[0][0] = 1, w3[0] = 2, b3 = 0.5
+    w[0] = 1.0
+    w[192 + 32 + 0] = 1.0
+    w[192 + 32 + 1024 + 32 + 0] = 2.0
+    w[-1] = 0.5
+    x = np.array([[0.7, 1, 2, 3, 4, 5], [-0.4, 1, 1, 1, 1, 1]])
+    np.testing.assert_allclose(oracle_mod.mlp_forward(w, x), [2 * 0.7 + 0.5, 0.5], rtol=0, atol=1e-15)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("n", [9, 300])
+def test_learned_proposal_keeps_the_estimator_unbiased(oracle_mod, kind, n):
+    t, q, F, kw = _setup(oracle_mod, n, 500 + n, kind)
+    w = np.random.default_rng(n).normal(scale=0.5, size=oracle_mod.MLP_NPARAM)
+    mean, var = t.enumerate_learned(q, w, 0.1, **kw)
+    scale = np.maximum(np.abs(F), 1e-3 if kind == "winding" else 0.0)
+    assert np.all(np.abs(mean - F) <= 1e-12 * scale + 1e-15)
+    assert np.all(var >= -1e-12 * scale * scale)
+
+
+def test_features_are_translation_and_scale_invariant(oracle_mod):
+    rng = np.random.default_rng(1)
+    pts = rng.random((500, 3))
+    w = rng.uniform(0.5, 1.5, 500)
+    nv = rng.normal(size=(500, 3))
+    q = np.array([0.3, 0.7, 0.2])
+    t1 = oracle_mod.Tree(pts.astype(np.float32), w.astype(np.float32), nv.astype(np.float32))
+    # a power-of-two scale and a translation that keep the float32 points and codes exact
+    t2 = oracle_mod.Tree((pts * 4 + 8).astype(np.float32), w.astype(np.float32), nv.astype(np.float32))
+    e = t1.export()
+    for node in np.nonzero(e["nchild"])[0][:20]:
+        np.testing.assert_allclose(t1.child_features(node, q, True), t2.child_features(node, q * 4 + 8, True),
+                                   rtol=1e-5, atol=1e-5)
