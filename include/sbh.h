@@ -182,6 +182,43 @@ SBH_API sbh_status sbh_multi_plan_create(const sbh_tree* const* trees, const flo
 SBH_API sbh_status sbh_multi_plan_launch(const sbh_multi_plan* plan, void* stream);
 SBH_API void sbh_multi_plan_free(sbh_multi_plan* plan);
 
+/* Learned child proposal (the paper samples the path index uniformly and leaves importance
+ * sampling to future work, Sec. 3.3; this is the project's extension). A 6-32-32-1 ReLU network
+ * (SBH_MLP_PARAMS values: W1[32][6], b1[32], W2[32][32], b2[32], w3[32], b3) scores each child c
+ * of a node from query-relative features: ln(d_c/|B_c|), ln(m_c/m_T), ln(|B_c|/|B_T|),
+ * ln(d_c/d_T), and for dipoles |N_c|/m_c and cos(p_c - q, N_c). The pick probability is
+ * pi_c = 0.9 softmax(s)_c + 0.1 m_c/m_T (every pi_c > 0, so the estimator stays unbiased with
+ * p(I in T) the product of the pi's); nodes with more than 64 children pick by mass. Inference
+ * uses FP16 weights with FP32 accumulation; training keeps FP32 master weights (Adam). */
+#define SBH_MLP_PARAMS 1313
+typedef struct sbh_mlp sbh_mlp;
+/* New network with He-scaled normal weights drawn from `seed`, zero biases. Synchronises. */
+SBH_API sbh_status sbh_mlp_create(uint64_t seed, void* stream, sbh_mlp** out);
+/* Host [SBH_MLP_PARAMS] FP32 weights in/out (the FP16 inference copy follows). Synchronise.
+ * adam_step (may be NULL) receives the number of training steps taken, for resuming. */
+SBH_API sbh_status sbh_mlp_set_weights(sbh_mlp* net, const float* host_weights, void* stream);
+SBH_API sbh_status sbh_mlp_get_weights(const sbh_mlp* net, float* host_weights, int64_t* adam_step, void* stream);
+/* Scores of feature rows (device [n][6] -> device [n]) with the FP16 inference weights. */
+SBH_API sbh_status sbh_mlp_scores(const sbh_mlp* net, const float* feats, int64_t n, float* scores, void* stream);
+/* Training loss and its gradient in the FP32 master weights: the mean over decision sets s (rows
+ * offsets[s] .. offsets[s+1]-1, 2..64 rows each; device int64 offsets) of the cross-entropy between
+ * softmax(scores) and the set's targets normalised to sum 1. grad device [SBH_MLP_PARAMS], loss
+ * device [1]. */
+SBH_API sbh_status sbh_mlp_loss_grad(sbh_mlp* net, const float* feats, const float* targets, const int64_t* offsets,
+                                     int64_t n_sets, float* grad, float* loss, void* stream);
+/* Train on the residuals the tree itself produces: for each of the nq training queries (device,
+ * 1 <= nq <= 2^20) and each subdomain with 2..64 children, the target of child c is |R_c(q)|, the
+ * exact residual of its subtree (sum over its points minus its centre-of-mass term, FP64 on the
+ * GPU; at most 2^26 rows in all, else SBH_EINVAL). `steps` full-batch Adam steps with learning rate lr; losses (host [steps] or NULL) gets the
+ * loss before each step. Synchronises. */
+SBH_API sbh_status sbh_mlp_train(sbh_mlp* net, const sbh_tree* tree, const float* queries, int64_t nq,
+                                 sbh_kernel kernel, int32_t steps, float lr, float* losses, void* stream);
+/* sbh_eval with the learned proposal (one thread per query; same random stream layout). */
+SBH_API sbh_status sbh_eval_learned(const sbh_tree* tree, const sbh_mlp* net, const float* queries, int64_t nq,
+                                    sbh_kernel kernel, int32_t samples_per_subdomain, uint64_t seed,
+                                    const sbh_eval_opts* opts, float* out, void* stream);
+SBH_API void sbh_mlp_free(sbh_mlp* net);
+
 /* Deterministic Barnes-Hut (Algorithm 1) on the 8-ary tree: a node is used whole when it is a
  * single point or ||q - p_a|| / |B_a| >= beta = 1 / theta (theta = 0 gives the exact sum).
  * warp_vote = 1 takes the decision jointly for the 32 queries of a warp (a node is opened when

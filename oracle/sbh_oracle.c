@@ -917,7 +917,7 @@ SBHO_API double sbho_mlp_loss_grad(const double *w, const double *feats, const d
         for (int64_t i = 0; i < nc; ++i) z += exp(sc[i] - mx);
         for (int64_t r = r0; r < r1; ++r) {
             double pr = exp(sc[r - r0] - mx) / z;
-            double tr = targets[r] / tsum;
+            double tr = tsum > 0 ? targets[r] / tsum : 1.0 / (double)nc;  /* all-zero targets: no preference */
             loss -= tr * (sc[r - r0] - mx - log(z)) / (double)n_sets;
             double ds = (pr - tr) / (double)n_sets;  /* d loss / d score */
             double h1[MLP_H], h2[MLP_H], dh2[MLP_H], dh1[MLP_H];

@@ -105,8 +105,19 @@ def load_library():
         lib.sbh_tree_export.argtypes = [P, i32, C.POINTER(_Export)]
         lib.sbh_tree_free.argtypes = [P]
         lib.sbh_tree_free.restype = None
+        lib.sbh_mlp_create.argtypes = [C.c_uint64, P, C.POINTER(P)]
+        lib.sbh_mlp_set_weights.argtypes = [P, P, P]
+        lib.sbh_mlp_get_weights.argtypes = [P, P, P, P]
+        lib.sbh_mlp_scores.argtypes = [P, P, i64, P, P]
+        lib.sbh_mlp_loss_grad.argtypes = [P, P, P, P, i64, P, P, P]
+        lib.sbh_mlp_train.argtypes = [P, P, P, i64, _Kernel, i32, C.c_float, P, P]
+        lib.sbh_eval_learned.argtypes = [P, P, P, i64, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts), P, P]
+        lib.sbh_mlp_free.argtypes = [P]
+        lib.sbh_mlp_free.restype = None
         for f in ("sbh_build", "sbh_eval", "sbh_eval_count", "sbh_eval_grad", "sbh_eval_bh", "sbh_eval_brute",
-                  "sbh_tree_info", "sbh_tree_export"):
+                  "sbh_tree_info", "sbh_tree_export", "sbh_mlp_create", "sbh_mlp_set_weights",
+                  "sbh_mlp_get_weights", "sbh_mlp_scores", "sbh_mlp_loss_grad", "sbh_mlp_train",
+                  "sbh_eval_learned"):
             getattr(lib, f).restype = i32
         _lib = lib
         return lib
@@ -425,3 +436,109 @@ def sbh_tree_export(tree: Tree, which: int = 0) -> dict:
 
 def sbh_tree_free(tree: Tree) -> None:
     tree.free()
+
+
+MLP_PARAMS = 1313
+
+
+class Mlp:
+    """Owner of an sbh_mlp handle (the learned child proposal); freed with the object."""
+
+    def __init__(self, handle: int):
+        self._h = C.c_void_p(handle)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h is not None and self._h.value:
+            load_library().sbh_mlp_free(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def sbh_mlp_create(seed: int = 0, stream=None) -> Mlp:
+    """New 6-32-32-1 proposal network with weights drawn from `seed`."""
+    lib = load_library()
+    h = C.c_void_p()
+    _check(lib.sbh_mlp_create(C.c_uint64(int(seed) & (2**64 - 1)), _stream(stream), C.byref(h)))
+    return Mlp(h.value)
+
+
+def sbh_mlp_set_weights(net: Mlp, weights, stream=None) -> None:
+    """Load FP32 master weights (any array-like of MLP_PARAMS values)."""
+    import numpy as np
+    w = np.ascontiguousarray(np.asarray(weights, dtype=np.float32).reshape(-1))
+    if w.size != MLP_PARAMS:
+        raise ValueError(f"weights must hold {MLP_PARAMS} values")
+    _check(load_library().sbh_mlp_set_weights(net.handle, w.ctypes.data_as(C.c_void_p), _stream(stream)))
+
+
+def sbh_mlp_get_weights(net: Mlp, stream=None):
+    """Return (FP32 master weights as numpy [MLP_PARAMS], Adam steps taken)."""
+    import numpy as np
+    w = np.empty(MLP_PARAMS, dtype=np.float32)
+    step = C.c_int64(0)
+    _check(load_library().sbh_mlp_get_weights(net.handle, w.ctypes.data_as(C.c_void_p), C.byref(step),
+                                              _stream(stream)))
+    return w, int(step.value)
+
+
+def sbh_mlp_scores(net: Mlp, feats, out=None, stream=None):
+    """Scores of feature rows [n, 6] with the FP16 inference weights; returns [n]."""
+    torch = _torch()
+    n = int(feats.shape[0])
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device=feats.device)
+    _check(load_library().sbh_mlp_scores(net.handle, _dev(feats, "feats", 6), n, _dev(out, "out"), _stream(stream)))
+    return out
+
+
+def sbh_mlp_loss_grad(net: Mlp, feats, targets, offsets, stream=None):
+    """Mean set cross-entropy and its gradient in the master weights; returns (loss [1], grad [MLP_PARAMS])."""
+    torch = _torch()
+    if not (isinstance(offsets, torch.Tensor) and offsets.is_cuda and offsets.dtype == torch.int64
+            and offsets.is_contiguous()):
+        raise ValueError("offsets must be a contiguous int64 CUDA tensor")
+    n_sets = int(offsets.numel()) - 1
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device=feats.device)
+    loss = torch.empty(1, dtype=torch.float32, device=feats.device)
+    _check(load_library().sbh_mlp_loss_grad(net.handle, _dev(feats, "feats", 6), _dev(targets, "targets"),
+                                            C.c_void_p(offsets.data_ptr()), n_sets, _dev(grad, "grad"),
+                                            _dev(loss, "loss"), _stream(stream)))
+    return loss, grad
+
+
+def sbh_mlp_train(net: Mlp, tree: Tree, queries, kernel="coulomb", steps: int = 200, lr: float = 3e-3,
+                  stream=None, softening: float = 1e-3, alpha: float = 200.0, affine=(0.0, 0.0, 0.0)):
+    """Fit the proposal to the tree's own child residuals at training queries [nq, 3]; returns the
+    loss before each step (numpy [steps])."""
+    import numpy as np
+    losses = np.zeros(max(int(steps), 1), dtype=np.float32)
+    k = _kernel_arg(kernel, softening, alpha, affine)
+    _check(load_library().sbh_mlp_train(net.handle, tree.handle, _dev(queries, "queries", 3), int(queries.shape[0]),
+                                        k, int(steps), C.c_float(lr), losses.ctypes.data_as(C.c_void_p),
+                                        _stream(stream)))
+    return losses[:int(steps)]
+
+
+def sbh_eval_learned(tree: Tree, net: Mlp, queries, kernel="coulomb", samples_per_subdomain: int = 1,
+                     seed: int = 0, opts: EvalOpts | None = None, out=None, stream=None, softening: float = 1e-3,
+                     alpha: float = 200.0, affine=(0.0, 0.0, 0.0)):
+    """Estimate with the learned child proposal; returns out [nq]."""
+    torch = _torch()
+    nq = int(queries.shape[0])
+    if out is None:
+        out = torch.empty(nq, dtype=torch.float32, device=queries.device)
+    k = _kernel_arg(kernel, softening, alpha, affine)
+    _check(load_library().sbh_eval_learned(tree.handle, net.handle, _dev(queries, "queries", 3), nq, k,
+                                           int(samples_per_subdomain), C.c_uint64(int(seed) & (2**64 - 1)),
+                                           C.byref(opts) if opts is not None else None, _dev(out, "out"),
+                                           _stream(stream)))
+    return out

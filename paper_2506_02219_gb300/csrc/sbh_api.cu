@@ -8,11 +8,14 @@
 #include <string.h>
 
 #include <atomic>
+#include <cmath>
+#include <vector>
 #include <new>
 
 #include "sbh.h"
 #include "sbh_build.cuh"
 #include "sbh_eval.cuh"
+#include "sbh_learned.cuh"
 
 namespace sbh {
 static std::atomic<unsigned long long> g_launches{0};
@@ -331,6 +334,203 @@ void sbh_multi_plan_free(sbh_multi_plan* plan)
     sbh::dfree(plan->counter, nullptr);
     cudaStreamSynchronize(nullptr);
     delete plan;
+}
+
+}  // extern "C"
+
+struct sbh_mlp {
+    int device = 0;
+    sbh::MlpState M;
+};
+
+namespace {
+// deterministic host initialisation: He-scaled normals from splitmix64 + Box-Muller
+uint64_t splitmix64(uint64_t& x)
+{
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double unit_open(uint64_t& st) { return ((double)(splitmix64(st) >> 11) + 0.5) * (1.0 / 9007199254740992.0); }
+double normal(uint64_t& st)
+{
+    const double u = unit_open(st), v = unit_open(st);
+    return std::sqrt(-2.0 * std::log(u)) * std::cos(6.283185307179586 * v);
+}
+}  // namespace
+
+extern "C" {
+
+sbh_status sbh_mlp_create(uint64_t seed, void* stream, sbh_mlp** out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(SBH_EINVAL, "out is NULL");
+    *out = nullptr;
+    sbh_mlp* N = new (std::nothrow) sbh_mlp();
+    if (!N) return fail(SBH_ENOMEM, "host allocation failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaGetDevice(&N->device);
+    std::vector<float> w(sbh::kMlpParams, 0.0f);
+    uint64_t st = seed;
+    for (int i = 0; i < 32 * 6; ++i) w[i] = (float)(normal(st) * std::sqrt(2.0 / 6.0));
+    for (int i = 0; i < 32 * 32; ++i) w[224 + i] = (float)(normal(st) * std::sqrt(2.0 / 32.0));
+    for (int i = 0; i < 32; ++i) w[1280 + i] = (float)(normal(st) * std::sqrt(1.0 / 32.0));
+    cudaError_t e = sbh::mlp_alloc(N->M, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(N->M.w, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = sbh::mlp_sync_half(N->M, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        sbh::mlp_release(N->M, s);
+        delete N;
+        return cuda_fail(e, "sbh_mlp_create");
+    }
+    *out = N;
+    return SBH_OK;
+}
+
+sbh_status sbh_mlp_set_weights(sbh_mlp* net, const float* host_weights, void* stream)
+{
+    g_err[0] = 0;
+    if (!net || !host_weights) return fail(SBH_EINVAL, "net and weights must be non-NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(net->M.w, host_weights, sbh::kMlpParams * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = sbh::mlp_sync_half(net->M, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_mlp_set_weights");
+    return SBH_OK;
+}
+
+sbh_status sbh_mlp_get_weights(const sbh_mlp* net, float* host_weights, int64_t* adam_step, void* stream)
+{
+    g_err[0] = 0;
+    if (!net || !host_weights) return fail(SBH_EINVAL, "net and weights must be non-NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(host_weights, net->M.w, sbh::kMlpParams * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_mlp_get_weights");
+    if (adam_step) *adam_step = net->M.step;
+    return SBH_OK;
+}
+
+sbh_status sbh_mlp_scores(const sbh_mlp* net, const float* feats, int64_t n, float* scores, void* stream)
+{
+    g_err[0] = 0;
+    if (!net || n < 0) return fail(SBH_EINVAL, "net is NULL or n < 0");
+    if (n == 0) return SBH_OK;
+    if (!device_ptr(feats) || !device_ptr(scores)) return fail(SBH_EINVAL, "feats and scores must be device memory");
+    cudaError_t e = sbh::mlp_scores(net->M, feats, n, scores, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_mlp_scores");
+    return SBH_OK;
+}
+
+sbh_status sbh_mlp_loss_grad(sbh_mlp* net, const float* feats, const float* targets, const int64_t* offsets,
+                             int64_t n_sets, float* grad, float* loss, void* stream)
+{
+    g_err[0] = 0;
+    if (!net || n_sets < 1) return fail(SBH_EINVAL, "net is NULL or n_sets < 1");
+    if (!device_ptr(feats) || !device_ptr(targets) || !device_ptr(offsets) || !device_ptr(grad) || !device_ptr(loss))
+        return fail(SBH_EINVAL, "all buffers must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = sbh::mlp_loss_grad(net->M, feats, targets, offsets, n_sets, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(grad, net->M.grad, sbh::kMlpParams * sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(loss, net->M.loss, sizeof(float), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_mlp_loss_grad");
+    return SBH_OK;
+}
+
+sbh_status sbh_mlp_train(sbh_mlp* net, const sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel,
+                         int32_t steps, float lr, float* losses, void* stream)
+{
+    g_err[0] = 0;
+    if (!net || !tree || !tree->t4.built) return fail(SBH_EINVAL, "net or tree missing");
+    if (nq < 1 || nq > (1 << 20) || steps < 0 || !(lr > 0.0f)) return fail(SBH_EINVAL, "need 1 <= nq <= 2^20, steps >= 0, lr > 0");
+    sbh::KernelParams kp;
+    sbh_status st = check_kernel(kernel, &kp);
+    if (st != SBH_OK) return st;
+    if (kernel.kind == SBH_WINDING && !tree->has_normals)
+        return fail(SBH_EINVAL, "the winding-number kernel needs a tree built with normals");
+    if (!device_ptr(queries)) return fail(SBH_EINVAL, "queries must be device memory");
+    cudaStream_t s = (cudaStream_t)stream;
+    // decision sets: the subdomains with 2..64 children
+    const sbh::TreeCtrl& c = tree->host_ctrl4;
+    std::vector<uint32_t> meta(c.n_sub);
+    cudaError_t e = cudaMemcpyAsync(meta.data(), tree->t4.meta + c.first_sub, c.n_sub * sizeof(uint32_t),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_mlp_train");
+    std::vector<int32_t> nodes;
+    std::vector<int32_t> nch;
+    for (int32_t i = 0; i < c.n_sub; ++i) {
+        const uint32_t nc = sbh::meta_nchild(meta[i]);
+        if (nc >= 2 && nc <= 64) { nodes.push_back(c.first_sub + i); nch.push_back((int32_t)nc); }
+    }
+    if (nodes.empty()) return fail(SBH_EUNSUPPORTED, "the tree has no subdomain with 2..64 children to learn from");
+    const int64_t n_sets = nq * (int64_t)nodes.size();
+    std::vector<int64_t> off((size_t)n_sets + 1);
+    off[0] = 0;
+    for (int64_t j = 0, k = 0; j < nq; ++j)
+        for (size_t a = 0; a < nodes.size(); ++a, ++k) off[(size_t)k + 1] = off[(size_t)k] + nch[a];
+    const int64_t rows = off[(size_t)n_sets];
+    if (rows > (int64_t(1) << 26)) return fail(SBH_EINVAL, "training set too large: nq x (children of the subdomains) > 2^26");
+    float *feats = nullptr, *targets = nullptr;
+    int64_t* doff = nullptr;
+    int32_t* dnodes = nullptr;
+    e = sbh::dalloc((void**)&feats, rows * 6 * sizeof(float), s);
+    if (e == cudaSuccess) e = sbh::dalloc((void**)&targets, rows * sizeof(float), s);
+    if (e == cudaSuccess) e = sbh::dalloc((void**)&doff, off.size() * sizeof(int64_t), s);
+    if (e == cudaSuccess) e = sbh::dalloc((void**)&dnodes, nodes.size() * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(doff, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dnodes, nodes.data(), nodes.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = sbh::mlp_dataset(tree, queries, (int)nq, dnodes, (int)nodes.size(), doff, kp, feats, targets, s);
+    for (int32_t k = 0; k < steps && e == cudaSuccess; ++k) {
+        e = sbh::mlp_loss_grad(net->M, feats, targets, doff, n_sets, s);
+        if (e == cudaSuccess && losses) e = cudaMemcpyAsync(&losses[k], net->M.loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = sbh::mlp_adam_step(net->M, lr, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host copies of `losses` (pageable) are complete
+    sbh::dfree(feats, s);
+    sbh::dfree(targets, s);
+    sbh::dfree(doff, s);
+    sbh::dfree(dnodes, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_mlp_train");
+    return SBH_OK;
+}
+
+sbh_status sbh_eval_learned(const sbh_tree* tree, const sbh_mlp* net, const float* queries, int64_t nq,
+                            sbh_kernel kernel, int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
+                            float* out, void* stream)
+{
+    g_err[0] = 0;
+    if (!tree || !tree->t4.built || !net) return fail(SBH_EINVAL, "tree or net missing");
+    if (nq < 0) return fail(SBH_EINVAL, "nq < 0");
+    if (samples_per_subdomain < 1) return fail(SBH_EINVAL, "samples_per_subdomain must be >= 1");
+    sbh::KernelParams kp;
+    sbh_status st = check_kernel(kernel, &kp);
+    if (st != SBH_OK) return st;
+    if (kernel.kind == SBH_WINDING && !tree->has_normals)
+        return fail(SBH_EINVAL, "the winding-number kernel needs a tree built with normals");
+    sbh_eval_opts o = {0, 0, 0, 0, 0};
+    if (opts) o = *opts;
+    if (!opts_ok(o)) return fail(SBH_EINVAL, "sbh_eval_opts out of range");
+    if (nq == 0) return SBH_OK;
+    if (!device_ptr(queries) || !device_ptr(out)) return fail(SBH_EINVAL, "queries and out must be device memory");
+    cudaError_t e = sbh::launch_stoch_learned(tree->t4.view(), net->M.wh, queries, nq, kp, samples_per_subdomain, seed,
+                                              o, out, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_eval_learned launch");
+    return SBH_OK;
+}
+
+void sbh_mlp_free(sbh_mlp* net)
+{
+    if (!net) return;
+    cudaDeviceSynchronize();
+    sbh::mlp_release(net->M, nullptr);
+    cudaStreamSynchronize(nullptr);
+    delete net;
 }
 
 unsigned long long sbh_kernel_launches(void) { return sbh::g_launches.load(std::memory_order_relaxed); }

@@ -23,6 +23,7 @@
 #include <stdint.h>
 
 #include "sbh_eval.cuh"
+#include "sbh_learned.cuh"
 
 namespace sbh {
 
@@ -31,6 +32,7 @@ namespace {
 constexpr int kModeCount = 0;
 constexpr int kModeGrad = 1;
 constexpr int kModeEval = 2;
+constexpr int kModeLearned = 3;  // evaluation with the learned child proposal
 
 // Running sum of weighted terms and of their query gradients. The smooth-distance kernel keeps
 // both in units of exp(-alpha ref), ref the smallest distance seen so far.
@@ -103,13 +105,18 @@ template <int KIND, int MODE>
 __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __restrict__ Q, int64_t nq,
                                                     KernelParams kp, int S, uint2 key, int sampling, int rr,
                                                     int coherent, int raw_sum, float* __restrict__ out,
-                                                    float* __restrict__ grad, unsigned long long* __restrict__ counts)
+                                                    float* __restrict__ grad, unsigned long long* __restrict__ counts,
+                                                    const __half* __restrict__ mlpw)
 {
     constexpr bool COUNT = MODE == kModeCount;
     constexpr bool GRAD = MODE == kModeGrad;
+    constexpr bool LEARNED = MODE == kModeLearned;
     Counters cnt;
     __shared__ float sdiam[kDiamLevels];
+    __shared__ __half sw[LEARNED ? kMlpParams : 1];
     if (threadIdx.x < kDiamLevels) sdiam[threadIdx.x] = T.ctrl->diam[threadIdx.x];
+    if (LEARNED)
+        for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) sw[i] = mlpw[i];
     __syncthreads();
     const int32_t first_sub = T.ctrl->first_sub;
     const int n_sub = T.ctrl->n_sub;
@@ -135,13 +142,17 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                 float dT = da;
                 float prr = 1.0f;
                 float wT = wa;
+                float ppath = 1.0f;  // learned proposal: probability of the picks so far
                 for (uint32_t depth = 0; meta_kind(mT) != kPoint && depth < (uint32_t)kMaxDepth; ++depth) {
                     const uint4 x = philox4x32_10(
                         make_uint4(coherent ? 0u : (uint32_t)j, (uint32_t)ai, (uint32_t)s, depth), key);
                     const int32_t f = __ldg(&T.fc[node]);
                     const int nc = (int)meta_nchild(mT);
                     int pick = 0;
-                    if (sampling == 0) {
+                    float pick_prob = 1.0f;
+                    if (LEARNED) {
+                        pick = learned_pick(T, sw, sdiam, node, mT, pT, q, KIND == SBH_WINDING, x.x, &pick_prob);
+                    } else if (sampling == 0) {
                         const float u = unit24(x.x);
                         for (int k = 0; k < nc - 1; ++k) pick += (__ldg(&T.cdf[f + k]) <= u) ? 1 : 0;
                     } else {
@@ -160,8 +171,9 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                     else p = (rr == 1) ? 1.0f : 0.5f;
                     if (unit24(x.y) >= p) break;
                     prr *= p;
-                    const float pagg = wT / wa;
+                    const float pagg = LEARNED ? ppath : wT / wa;
                     const float w = 1.0f / (pagg * prr) * invS;
+                    ppath *= pick_prob;
                     if (COUNT) {
                         cnt.evals += (uint64_t)nc + 1;
                         cnt.records += (uint64_t)nc;
@@ -210,7 +222,7 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
 template <int MODE>
 cudaError_t launch_lane_impl(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
                              uint64_t seed, const sbh_eval_opts& o, float* out, float* grad,
-                             unsigned long long* counts, cudaStream_t s)
+                             unsigned long long* counts, cudaStream_t s, const __half* mlpw = nullptr)
 {
     if (nq <= 0) return cudaSuccess;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -220,16 +232,16 @@ cudaError_t launch_lane_impl(const TreeView& T, const float* Q, int64_t nq, cons
     const unsigned b = (unsigned)blocks;
     switch (kp.kind) {
     case SBH_COULOMB:
-        k_stoch_eval<SBH_COULOMB, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts);
+        k_stoch_eval<SBH_COULOMB, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw);
         break;
     case SBH_WINDING:
-        k_stoch_eval<SBH_WINDING, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts);
+        k_stoch_eval<SBH_WINDING, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw);
         break;
     case SBH_SMOOTHDIST:
-        k_stoch_eval<SBH_SMOOTHDIST, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts);
+        k_stoch_eval<SBH_SMOOTHDIST, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw);
         break;
     case SBH_AFFINE:
-        k_stoch_eval<SBH_AFFINE, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts);
+        k_stoch_eval<SBH_AFFINE, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw);
         break;
     default:
         return cudaErrorInvalidValue;
@@ -252,6 +264,14 @@ cudaError_t launch_stoch_lane(const TreeView& T, const float* Q, int64_t nq, con
                               uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s)
 {
     return launch_lane_impl<kModeEval>(T, Q, nq, kp, S, seed, o, out, nullptr, nullptr, s);
+}
+
+cudaError_t launch_stoch_learned(const TreeView& T, const void* mlp_half, const float* Q, int64_t nq,
+                                 const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
+                                 cudaStream_t s)
+{
+    return launch_lane_impl<kModeLearned>(T, Q, nq, kp, S, seed, o, out, nullptr, nullptr, s,
+                                          (const __half*)mlp_half);
 }
 
 cudaError_t launch_stoch_count(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,

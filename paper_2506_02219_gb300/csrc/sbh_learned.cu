@@ -1,0 +1,313 @@
+// sbh_learned.cu -- the learned child proposal: a 6-32-32-1 ReLU network that scores each child
+// of a node from query-relative geometry, trained on the residuals the estimator's own tree
+// produces, and used in place of the mass-proportional pick of Algorithm 2.
+//
+// The paper samples the path index uniformly and names importance sampling as future work
+// (Sec. 3.3); this is the project's extension. The proposal at node T is
+//   pi_c = (1 - eps) softmax(s)_c + eps m_c / m_T,   eps = 0.1,
+// so every child keeps a probability >= eps m_c / m_T > 0 and the estimator stays unbiased with
+// p(I in T) the product of the pi's along the path. Nodes with more than 64 children use the
+// mass-proportional pick. Inference reads FP16 weights and accumulates in FP32; training keeps
+// FP32 master weights (Adam) and targets pi*_c proportional to |R_c(q)|, the exact residual of
+// child c's subtree (its exact sum minus its centre-of-mass term), which is the per-level
+// proposal that minimises the variance of the child's contribution.
+//
+// Parameter layout (1313 values): W1[32][6], b1[32], W2[32][32], b2[32], w3[32], b3.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sbh_build.cuh"
+#include "sbh_learned.cuh"
+
+namespace sbh {
+
+namespace {
+
+__global__ void k_scores(const __half* __restrict__ wg, const float* __restrict__ feats, int64_t n,
+                         float* __restrict__ out)
+{
+    __shared__ __half w[kMlpParams];
+    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) w[i] = wg[i];
+    __syncthreads();
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        float x[6];
+        for (int k = 0; k < 6; ++k) x[k] = feats[6 * r + k];
+        out[r] = score16(w, x);
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// training set: for every training query and every subdomain a with 2..64 children, one decision
+// set = the children of a, features and |exact residual| targets (FP64 sums over the child's
+// points, in Morton order)
+// ------------------------------------------------------------------------------------------------
+template <int KIND>
+__device__ __forceinline__ double point_value(float4 p, const float4* nrm, int64_t i, float3 q, const KernelParams& kp)
+{
+    const double dx = (double)p.x - q.x, dy = (double)p.y - q.y, dz = (double)p.z - q.z;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if constexpr (KIND == SBH_COULOMB) return (double)p.w / sqrt(r2 + (double)kp.eps2);
+    else if constexpr (KIND == SBH_WINDING) {
+        if (r2 == 0.0) return 0.0;
+        const float4 n = nrm[i];
+        return (double)p.w * (dx * n.x + dy * n.y + dz * n.z) / (4.0 * 3.141592653589793 * r2 * sqrt(r2));
+    } else if constexpr (KIND == SBH_SMOOTHDIST) {
+        return (double)p.w * exp(-(double)kp.alpha * sqrt(r2));
+    } else {
+        return (double)p.w * (1.0 + kp.g[0] * dx + kp.g[1] * dy + kp.g[2] * dz);
+    }
+}
+
+template <int KIND>
+__device__ __forceinline__ double node_value64(const TreeView& T, int32_t v, float4 pm, float3 q, const KernelParams& kp)
+{
+    const double dx = (double)pm.x - q.x, dy = (double)pm.y - q.y, dz = (double)pm.z - q.z;
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if constexpr (KIND == SBH_COULOMB) return (double)pm.w / sqrt(r2 + (double)kp.eps2);
+    else if constexpr (KIND == SBH_WINDING) {
+        if (r2 == 0.0) return 0.0;
+        const float4 N = __ldg(&T.dip[v]);
+        return (dx * N.x + dy * N.y + dz * N.z) / (4.0 * 3.141592653589793 * r2 * sqrt(r2));
+    } else if constexpr (KIND == SBH_SMOOTHDIST) {
+        return (double)pm.w * exp(-(double)kp.alpha * sqrt(r2));
+    } else {
+        return (double)pm.w * (1.0 + kp.g[0] * dx + kp.g[1] * dy + kp.g[2] * dz);
+    }
+}
+
+// one warp per (query, subdomain set); set s covers rows set_off[s] .. set_off[s+1]-1
+template <int KIND>
+__global__ void k_dataset(TreeView T, const float4* __restrict__ spw, const float4* __restrict__ snrm,
+                          const float* __restrict__ Q, int nq, const int32_t* __restrict__ set_node, int n_node_sets,
+                          const int64_t* __restrict__ set_off, KernelParams kp, float* __restrict__ feats,
+                          float* __restrict__ targets)
+{
+    __shared__ float diam[kDiamLevels];
+    if (threadIdx.x < kDiamLevels) diam[threadIdx.x] = T.ctrl->diam[threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t n_sets = (int64_t)nq * n_node_sets;
+    for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n_sets;
+         s += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t j = s / n_node_sets;
+        const int32_t a = set_node[s % n_node_sets];
+        const float3 q = make_float3(Q[3 * j], Q[3 * j + 1], Q[3 * j + 2]);
+        const uint32_t ma = __ldg(&T.meta[a]);
+        const float4 pa = __ldg(&T.pm[a]);
+        const int32_t f = __ldg(&T.fc[a]);
+        const int nc = (int)meta_nchild(ma);
+        const int64_t r0 = set_off[s];
+        for (int c = 0; c < nc; ++c) {
+            const int32_t ch = f + c;
+            const int32_t b = __ldg(&T.nb[ch]), e = __ldg(&T.ne[ch]);
+            double sum = 0.0;
+            for (int32_t i = b + lane; i < e; i += 32) sum += point_value<KIND>(spw[i], snrm, i, q, kp);
+            for (int off = 16; off > 0; off >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, off);
+            if (lane == 0) {
+                const float4 pc = __ldg(&T.pm[ch]);
+                const double r = sum - node_value64<KIND>(T, ch, pc, q, kp);
+                targets[r0 + c] = (float)fabs(r);
+                float x[6];
+                child_features(T, diam, ma, pa, ch, pc, __ldg(&T.meta[ch]), q, KIND == SBH_WINDING, x);
+                for (int k = 0; k < 6; ++k) feats[6 * (r0 + c) + k] = x[k];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// loss and gradient: mean over sets of the cross-entropy between softmax(scores) and the set's
+// normalised targets. One warp per set, lane i = hidden unit i of both layers; per-lane partial
+// gradients (its rows of W1 and W2 and its biases) are added to the global gradient at the end.
+// ------------------------------------------------------------------------------------------------
+constexpr int kTrainWarps = 4;
+
+__global__ void __launch_bounds__(32 * kTrainWarps) k_loss_grad(const float* __restrict__ wg,
+                                                               const float* __restrict__ feats,
+                                                               const float* __restrict__ targets,
+                                                               const int64_t* __restrict__ off, int64_t n_sets,
+                                                               float inv_sets, float* __restrict__ grad,
+                                                               float* __restrict__ loss)
+{
+    __shared__ float w[kMlpParams];
+    __shared__ float sc[kTrainWarps][kMaxLearnedChildren];
+    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) w[i] = wg[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float gW1[kIn] = {0, 0, 0, 0, 0, 0}, gW2[kH], gb1 = 0, gb2 = 0, gw3 = 0, gb3 = 0, lsum = 0;
+    for (int k = 0; k < kH; ++k) gW2[k] = 0.0f;
+    const float b1 = w[ob1 + lane], b2 = w[ob2 + lane], w3 = w[ow3 + lane], b3 = w[ob3];
+
+    for (int64_t s = (int64_t)blockIdx.x * kTrainWarps + warp; s < n_sets; s += (int64_t)gridDim.x * kTrainWarps) {
+        const int64_t r0 = off[s];
+        const int nc = (int)(off[s + 1] - r0);
+        if (nc < 2 || nc > kMaxLearnedChildren) continue;
+        // forward: scores
+        float tsum = 0.0f;
+        for (int c = 0; c < nc; ++c) {
+            const float* x = feats + 6 * (r0 + c);
+            float z = b1;
+            for (int k = 0; k < kIn; ++k) z = fmaf(w[oW1 + lane * kIn + k], x[k], z);
+            const float h1 = fmaxf(z, 0.0f);
+            float z2 = b2;
+            for (int k = 0; k < kH; ++k) z2 = fmaf(w[oW2 + lane * kH + k], __shfl_sync(0xFFFFFFFFu, h1, k), z2);
+            float t = w3 * fmaxf(z2, 0.0f);
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
+            if (lane == 0) sc[warp][c] = t + b3;
+            tsum += targets[r0 + c];
+        }
+        __syncwarp();
+        float mx = -3.0e38f;
+        for (int c = 0; c < nc; ++c) mx = fmaxf(mx, sc[warp][c]);
+        float Z = 0.0f;
+        for (int c = 0; c < nc; ++c) Z += __expf(sc[warp][c] - mx);
+        const float logZ = __logf(Z);
+        const float tnorm = tsum > 0.0f ? 1.0f / tsum : 0.0f;
+        // backward, recomputing each row's activations
+        for (int c = 0; c < nc; ++c) {
+            const float* x = feats + 6 * (r0 + c);
+            const float t = tsum > 0.0f ? targets[r0 + c] * tnorm : 1.0f / nc;
+            const float lp = sc[warp][c] - mx - logZ;
+            if (lane == 0) lsum -= t * lp;
+            const float ds = (__expf(lp) - t) * inv_sets;
+            float z = b1;
+            for (int k = 0; k < kIn; ++k) z = fmaf(w[oW1 + lane * kIn + k], x[k], z);
+            const float h1 = fmaxf(z, 0.0f);
+            float z2 = b2;
+            for (int k = 0; k < kH; ++k) z2 = fmaf(w[oW2 + lane * kH + k], __shfl_sync(0xFFFFFFFFu, h1, k), z2);
+            const float h2 = fmaxf(z2, 0.0f);
+            gw3 = fmaf(ds, h2, gw3);
+            if (lane == 0) gb3 += ds;
+            const float dh2 = z2 > 0.0f ? ds * w3 : 0.0f;
+            gb2 += dh2;
+            float dh1 = 0.0f;
+            for (int k = 0; k < kH; ++k) {
+                const float h1k = __shfl_sync(0xFFFFFFFFu, h1, k);
+                gW2[k] = fmaf(dh2, h1k, gW2[k]);
+                // dh1 of unit `lane`: sum_i W2[i][lane] dh2_i
+                dh1 = fmaf(w[oW2 + k * kH + lane], __shfl_sync(0xFFFFFFFFu, dh2, k), dh1);
+            }
+            dh1 = z > 0.0f ? dh1 : 0.0f;
+            gb1 += dh1;
+            for (int k = 0; k < kIn; ++k) gW1[k] = fmaf(dh1, x[k], gW1[k]);
+        }
+        __syncwarp();
+    }
+    for (int k = 0; k < kIn; ++k) atomicAdd(&grad[oW1 + lane * kIn + k], gW1[k]);
+    atomicAdd(&grad[ob1 + lane], gb1);
+    for (int k = 0; k < kH; ++k) atomicAdd(&grad[oW2 + lane * kH + k], gW2[k]);
+    atomicAdd(&grad[ob2 + lane], gb2);
+    atomicAdd(&grad[ow3 + lane], gw3);
+    if (lane == 0) {
+        atomicAdd(&grad[ob3], gb3);
+        atomicAdd(loss, lsum * inv_sets);
+    }
+}
+
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       __half* __restrict__ wh, float lr, float c1, float c2)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMlpParams) return;
+    const float gi = g[i];
+    const float mi = 0.9f * m[i] + 0.1f * gi;
+    const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+    w[i] = wi;
+    wh[i] = __float2half_rn(wi);
+}
+
+__global__ void k_to_half(const float* __restrict__ w, __half* __restrict__ wh)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < kMlpParams) wh[i] = __float2half_rn(w[i]);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------------
+cudaError_t mlp_alloc(MlpState& M, cudaStream_t s)
+{
+    cudaError_t e = dalloc((void**)&M.w, kMlpParams * sizeof(float), s);
+    if (e == cudaSuccess) e = dalloc((void**)&M.wh, kMlpParams * sizeof(__half), s);
+    if (e == cudaSuccess) e = dalloc((void**)&M.m, kMlpParams * sizeof(float), s);
+    if (e == cudaSuccess) e = dalloc((void**)&M.v, kMlpParams * sizeof(float), s);
+    if (e == cudaSuccess) e = dalloc((void**)&M.grad, kMlpParams * sizeof(float), s);
+    if (e == cudaSuccess) e = dalloc((void**)&M.loss, sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M.m, 0, kMlpParams * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M.v, 0, kMlpParams * sizeof(float), s);
+    return e;
+}
+
+void mlp_release(MlpState& M, cudaStream_t s)
+{
+    dfree(M.w, s); dfree(M.wh, s); dfree(M.m, s); dfree(M.v, s); dfree(M.grad, s); dfree(M.loss, s);
+    M = MlpState();
+}
+
+cudaError_t mlp_sync_half(MlpState& M, cudaStream_t s)
+{
+    k_to_half<<<(kMlpParams + 255) / 256, 256, 0, s>>>(M.w, M.wh);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_scores(const MlpState& M, const float* feats, int64_t n, float* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_scores<<<(unsigned)blocks, 256, 0, s>>>(M.wh, feats, n, out);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_loss_grad(MlpState& M, const float* feats, const float* targets, const int64_t* off, int64_t n_sets,
+                          cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(M.grad, 0, kMlpParams * sizeof(float), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M.loss, 0, sizeof(float), s);
+    if (e != cudaSuccess || n_sets <= 0) return e;
+    int64_t blocks = (n_sets + kTrainWarps - 1) / kTrainWarps;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_loss_grad<<<(unsigned)blocks, 32 * kTrainWarps, 0, s>>>(M.w, feats, targets, off, n_sets, 1.0f / (float)n_sets,
+                                                             M.grad, M.loss);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_adam_step(MlpState& M, float lr, cudaStream_t s)
+{
+    M.step += 1;
+    const float c1 = 1.0f / (1.0f - powf(0.9f, (float)M.step));
+    const float c2 = 1.0f / (1.0f - powf(0.999f, (float)M.step));
+    k_adam<<<(kMlpParams + 255) / 256, 256, 0, s>>>(M.w, M.grad, M.m, M.v, M.wh, lr, c1, c2);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_dataset(const sbh_tree* tree, const float* Q, int nq, const int32_t* set_node, int n_node_sets,
+                        const int64_t* set_off, const KernelParams& kp, float* feats, float* targets, cudaStream_t s)
+{
+    const TreeView T = tree->t4.view();
+    const int64_t warps = (int64_t)nq * n_node_sets;
+    int64_t blocks = (warps * 32 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    const unsigned b = (unsigned)(blocks < 1 ? 1 : blocks);
+    switch (kp.kind) {
+    case SBH_COULOMB: k_dataset<SBH_COULOMB><<<b, 256, 0, s>>>(T, tree->spw, tree->snrm, Q, nq, set_node, n_node_sets, set_off, kp, feats, targets); break;
+    case SBH_WINDING: k_dataset<SBH_WINDING><<<b, 256, 0, s>>>(T, tree->spw, tree->snrm, Q, nq, set_node, n_node_sets, set_off, kp, feats, targets); break;
+    case SBH_SMOOTHDIST: k_dataset<SBH_SMOOTHDIST><<<b, 256, 0, s>>>(T, tree->spw, tree->snrm, Q, nq, set_node, n_node_sets, set_off, kp, feats, targets); break;
+    case SBH_AFFINE: k_dataset<SBH_AFFINE><<<b, 256, 0, s>>>(T, tree->spw, tree->snrm, Q, nq, set_node, n_node_sets, set_off, kp, feats, targets); break;
+    default: return cudaErrorInvalidValue;
+    }
+    note_launch();
+    return cudaGetLastError();
+}
+
+}  // namespace sbh

@@ -65,3 +65,14 @@ def test_features_are_translation_and_scale_invariant(oracle_mod):
     for node in np.nonzero(e["nchild"])[0][:20]:
         np.testing.assert_allclose(t1.child_features(node, q, True), t2.child_features(node, q * 4 + 8, True),
                                    rtol=1e-5, atol=1e-5)
+
+
+def test_all_zero_targets_mean_no_preference(oracle_mod):
+    # a decision set whose children all have zero residual gets uniform targets: with a network
+    # that scores every child alike, the cross-entropy is log(nc) and the gradient vanishes
+    w = np.zeros(oracle_mod.MLP_NPARAM)
+    w[-1] = 0.3
+    x = np.random.default_rng(2).normal(size=(7, 6))
+    loss, g = oracle_mod.mlp_loss_grad(w, x, np.zeros(7), [0, 7])
+    assert abs(loss - np.log(7)) <= 1e-15
+    assert np.all(np.abs(g) <= 1e-15)
