@@ -92,7 +92,7 @@ def _load():
         lib.sbho_mlp_loss_grad.argtypes = [P, P, P, P, i64, P]
         lib.sbho_mlp_loss_grad.restype = C.c_double
         lib.sbho_child_features.argtypes = [P, i64, P, i32, P]
-        lib.sbho_enumerate_learned.argtypes = [P, C.POINTER(_Kernel), P, C.c_double, P, i64, P, P]
+        lib.sbho_enumerate_learned.argtypes = [P, C.POINTER(_Kernel), P, C.c_double, C.c_float, P, i64, P, P]
         lib.sbho_max_threads.restype = i32
         lib.sbho_set_threads.argtypes = [i32]
         _lib = lib
@@ -283,14 +283,16 @@ class Tree:
         return x
 
     def enumerate_learned(self, queries, weights, eps: float = 0.1, kind=COULOMB, softening=1e-3, alpha=200.0,
-                          affine=(0.0, 0.0, 0.0)):
-        """Exact (mean, variance) of the one-sample estimator with the learned proposal."""
+                          affine=(0.0, 0.0, 0.0), near: float = float("inf")):
+        """Exact (mean, variance) of the one-sample estimator with the learned proposal, used at
+        nodes with at most 64 children nearer to the query than `near` cell diagonals."""
         q = _f32(queries, 3)
         w = np.ascontiguousarray(np.asarray(weights, np.float64))
         mean = np.zeros(q.shape[0], np.float64)
         var = np.zeros(q.shape[0], np.float64)
         k = kernel(kind, softening, alpha, affine)
-        self._lib.sbho_enumerate_learned(self._h, C.byref(k), _ptr(w), C.c_double(eps), _ptr(q), q.shape[0],
+        self._lib.sbho_enumerate_learned(self._h, C.byref(k), _ptr(w), C.c_double(eps), C.c_float(near), _ptr(q),
+                                         q.shape[0],
                                          _ptr(mean), _ptr(var))
         return mean, var
 

@@ -944,20 +944,32 @@ SBHO_API double sbho_mlp_loss_grad(const double *w, const double *feats, const d
     return loss;
 }
 
-/* proposal probabilities of the children of T: (1 - eps) softmax(scores) + eps m_c / m_T */
-static void learned_probs(const otree *t, const double *w, double eps, int use_dipole, int64_t T, const double q[3],
-                          double *pi)
+/* Proposal probabilities of the children of T. Where the network is used -- at most 64 children
+ * and the query nearer than `near` cell diagonals, d_T < near |B_T| (FP32, the same test as the
+ * GPU's) -- pi_c = (1 - eps) softmax(s)_c + eps m_c / m_T with the scores clamped to [-40, 40];
+ * elsewhere the mass proportion m_c / m_T. Any proposal with every pi_c > 0 keeps the estimator
+ * unbiased (Appendix A with p_agg the product of the pi's along the path). */
+#define MLP_MAX_CHILDREN 64
+#define MLP_SCORE_CLAMP 40.0
+static void learned_probs(const otree *t, const double *w, double eps, int use_dipole, float near, int64_t T,
+                          const double q[3], const float q32[3], double *pi)
 {
     int nc = t->nchild[T];
     int64_t fc = t->first_child[T];
-    double mx = -1e300, z = 0, mt = 0, x[6];
+    double z = 0, mt = 0, x[6];
+    for (int c = 0; c < nc; ++c) mt += t->mass[fc + c];
+    const float reach = near * diam32(t, t->level[T]);
+    if (nc > MLP_MAX_CHILDREN || !(dist32(&t->com32[3 * T], q32) < reach)) {
+        for (int c = 0; c < nc; ++c) pi[c] = t->mass[fc + c] / mt;
+        return;
+    }
     for (int c = 0; c < nc; ++c) {
         child_features(t, T, fc + c, q, use_dipole, x);
-        pi[c] = mlp_score(w, x, NULL, NULL);
-        if (pi[c] > mx) mx = pi[c];
-        mt += t->mass[fc + c];
+        double sc = mlp_score(w, x, NULL, NULL);
+        sc = sc < -MLP_SCORE_CLAMP ? -MLP_SCORE_CLAMP : (sc > MLP_SCORE_CLAMP ? MLP_SCORE_CLAMP : sc);
+        pi[c] = exp(sc);
+        z += pi[c];
     }
-    for (int c = 0; c < nc; ++c) { pi[c] = exp(pi[c] - mx); z += pi[c]; }
     for (int c = 0; c < nc; ++c) pi[c] = (1.0 - eps) * pi[c] / z + eps * t->mass[fc + c] / mt;
 }
 
@@ -970,14 +982,15 @@ SBHO_API void sbho_child_features(const void *h, int64_t T, const float *q32, in
 }
 
 /* exact mean and variance of the one-sample estimator with the learned proposal */
-static void enum_learned_rec(const otree *t, const sbho_kernel *k, const double *w, double eps, int64_t T,
-                             const double q[3], double P, double V, double ppath, double prr, moments *acc)
+static void enum_learned_rec(const otree *t, const sbho_kernel *k, const double *w, double eps, float near,
+                             int64_t T, const double q[3], const float q32[3], double P, double V, double ppath,
+                             double prr, moments *acc)
 {
     if (t->nchild[T] == 0) { acc->e1 += P * V; acc->e2 += P * V * V; return; }
     double delta = swap_delta(t, k, T, q);
     int nc = t->nchild[T];
     double *pi = (double *)malloc(sizeof(double) * (size_t)nc);
-    learned_probs(t, w, eps, k->kind == K_WINDING, T, q, pi);
+    learned_probs(t, w, eps, k->kind == K_WINDING, near, T, q, q32, pi);
     for (int c = 0; c < nc; ++c) {
         int64_t ch = t->first_child[T] + c;
         double p = rr_prob64(t, T, ch, q, RR_PAPER);
@@ -985,22 +998,24 @@ static void enum_learned_rec(const otree *t, const sbho_kernel *k, const double 
         acc->e1 += Pstop * V;
         acc->e2 += Pstop * V * V;
         double prr2 = prr * p;
-        enum_learned_rec(t, k, w, eps, ch, q, P * pi[c] * p, V + delta / (ppath * prr2), ppath * pi[c], prr2, acc);
+        enum_learned_rec(t, k, w, eps, near, ch, q, q32, P * pi[c] * p, V + delta / (ppath * prr2), ppath * pi[c],
+                         prr2, acc);
     }
     free(pi);
 }
 
-SBHO_API void sbho_enumerate_learned(const void *h, const sbho_kernel *k, const double *w, double eps,
+SBHO_API void sbho_enumerate_learned(const void *h, const sbho_kernel *k, const double *w, double eps, float near,
                                      const float *queries, int64_t nq, double *mean, double *var)
 {
     const otree *t = (const otree *)h;
     for (int64_t j = 0; j < nq; ++j) {
         double q[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
+        const float *q32 = &queries[3 * j];
         double E = 0, Var = 0;
         for (int64_t ai = 0; ai < t->n_sub; ++ai) {
             int64_t a = t->first_sub + ai;
             moments m = {0, 0};
-            enum_learned_rec(t, k, w, eps, a, q, 1.0, 0.0, 1.0, 1.0, &m);
+            enum_learned_rec(t, k, w, eps, near, a, q, q32, 1.0, 0.0, 1.0, 1.0, &m);
             E += node_term(t, k, a, q) + m.e1;
             Var += m.e2 - m.e1 * m.e1;
         }

@@ -43,10 +43,11 @@ def test_hand_built_network(oracle_mod):
 
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("n", [9, 300])
-def test_learned_proposal_keeps_the_estimator_unbiased(oracle_mod, kind, n):
+@pytest.mark.parametrize("near", [np.inf, 1.0])
+def test_learned_proposal_keeps_the_estimator_unbiased(oracle_mod, kind, n, near):
     t, q, F, kw = _setup(oracle_mod, n, 500 + n, kind)
     w = np.random.default_rng(n).normal(scale=0.5, size=oracle_mod.MLP_NPARAM)
-    mean, var = t.enumerate_learned(q, w, 0.1, **kw)
+    mean, var = t.enumerate_learned(q, w, 0.1, near=near, **kw)
     scale = np.maximum(np.abs(F), 1e-3 if kind == "winding" else 0.0)
     assert np.all(np.abs(mean - F) <= 1e-12 * scale + 1e-15)
     assert np.all(var >= -1e-12 * scale * scale)
@@ -76,3 +77,27 @@ def test_all_zero_targets_mean_no_preference(oracle_mod):
     loss, g = oracle_mod.mlp_loss_grad(w, x, np.zeros(7), [0, 7])
     assert abs(loss - np.log(7)) <= 1e-15
     assert np.all(np.abs(g) <= 1e-15)
+
+
+@pytest.mark.parametrize("kind", ["coulomb", "winding"])
+def test_gate_closed_everywhere_is_the_mass_proposal(oracle_mod, kind):
+    # near = 0: no node is near enough, every pick is mass-proportional and p(I in T) is the
+    # product of the mass fractions, m_T / m_a: the variance is that of Algorithm 2 with mass p_agg
+    t, q, F, kw = _setup(oracle_mod, 300, 77, kind)
+    w = np.random.default_rng(3).normal(scale=0.5, size=oracle_mod.MLP_NPARAM)
+    mean_l, var_l = t.enumerate_learned(q, w, 0.1, near=0.0, **kw)
+    mean_m, var_m = t.enumerate(q, **kw)
+    np.testing.assert_allclose(mean_l, mean_m, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(var_l, var_m, rtol=1e-9, atol=1e-12 * np.max(np.abs(F)) ** 2)
+
+
+def test_gate_changes_the_variance_only_near_the_query(oracle_mod):
+    # a query far from every subdomain (more than 1 diagonal away) sees the mass proposal for near = 1
+    t, q, F, kw = _setup(oracle_mod, 300, 78, "coulomb")
+    far = np.array([[9.0, 9.0, 9.0]], np.float32)
+    w = np.random.default_rng(4).normal(scale=0.5, size=oracle_mod.MLP_NPARAM)
+    _, v1 = t.enumerate_learned(far, w, 0.1, near=1.0, **kw)
+    _, vm = t.enumerate(far, **kw)
+    _, vi = t.enumerate_learned(far, w, 0.1, **kw)
+    np.testing.assert_allclose(v1, vm, rtol=1e-9)
+    assert abs(vi[0] - vm[0]) > 1e-6 * vm[0]
