@@ -198,7 +198,8 @@ SBH_API sbh_status sbh_mlp_create(uint64_t seed, void* stream, sbh_mlp** out);
  * adam_step (may be NULL) receives the number of training steps taken, for resuming. */
 SBH_API sbh_status sbh_mlp_set_weights(sbh_mlp* net, const float* host_weights, void* stream);
 SBH_API sbh_status sbh_mlp_get_weights(const sbh_mlp* net, float* host_weights, int64_t* adam_step, void* stream);
-/* Scores of feature rows (device [n][6] -> device [n]) with the FP16 inference weights. */
+/* Scores of feature rows (device [n][6] -> device [n]) with the estimator's tensor-core scorer
+ * (FP16 features, weights and hidden activations; FP32 accumulation). */
 SBH_API sbh_status sbh_mlp_scores(const sbh_mlp* net, const float* feats, int64_t n, float* scores, void* stream);
 /* Training loss and its gradient in the FP32 master weights: the mean over decision sets s (rows
  * offsets[s] .. offsets[s+1]-1, 2..64 rows each; device int64 offsets) of the cross-entropy between
@@ -206,17 +207,32 @@ SBH_API sbh_status sbh_mlp_scores(const sbh_mlp* net, const float* feats, int64_
  * device [1]. */
 SBH_API sbh_status sbh_mlp_loss_grad(sbh_mlp* net, const float* feats, const float* targets, const int64_t* offsets,
                                      int64_t n_sets, float* grad, float* loss, void* stream);
-/* Train on the residuals the tree itself produces: for each of the nq training queries (device,
- * 1 <= nq <= 2^20) and each subdomain with 2..64 children, the target of child c is |R_c(q)|, the
- * exact residual of its subtree (sum over its points minus its centre-of-mass term, FP64 on the
- * GPU; at most 2^26 rows in all, else SBH_EINVAL). `steps` full-batch Adam steps with learning rate lr; losses (host [steps] or NULL) gets the
- * loss before each step. Synchronises. */
+/* Training rows of explicit decision sets: set s is node set_node[s] at query set_query[s]
+ * (device int32, queries device [.][3]); its rows set_offsets[s] .. set_offsets[s+1]-1 (device int64,
+ * n_sets + 1 entries, set_offsets[s+1] - set_offsets[s] = the node's child count) receive each
+ * child's features (feats, device [rows][6]) and target |R_c(q)|, the exact residual of the child's
+ * subtree: the FP64 sum over its points minus its own centre-of-mass term (targets, device [rows]). */
+SBH_API sbh_status sbh_mlp_dataset(const sbh_tree* tree, const float* queries, sbh_kernel kernel,
+                                   const int32_t* set_query, const int32_t* set_node, const int64_t* set_offsets,
+                                   int64_t n_sets, float* feats, float* targets, void* stream);
+/* Train on the residuals the method itself produces: each of the nq training queries (device,
+ * 1 <= nq <= 2^20) walks 4 paths of Algorithm 2 per subdomain (mass picks, Eq. 5 roulette, a
+ * fixed training stream) and every node it decides at where the network is used (2..64 children,
+ * d_T < near |B_T|; at most 4096 per query) becomes a decision set (sbh_mlp_dataset); at most 2^26
+ * rows in all, else SBH_EINVAL; SBH_EUNSUPPORTED if there is none. Then `steps` full-batch Adam
+ * steps with learning rate lr; losses (host [steps] or NULL) gets the loss before each step.
+ * Synchronises. */
 SBH_API sbh_status sbh_mlp_train(sbh_mlp* net, const sbh_tree* tree, const float* queries, int64_t nq,
-                                 sbh_kernel kernel, int32_t steps, float lr, float* losses, void* stream);
-/* sbh_eval with the learned proposal (one thread per query; same random stream layout). */
+                                 sbh_kernel kernel, float near, int32_t steps, float lr, float* losses, void* stream);
+/* sbh_eval with the learned proposal, used at nodes with 2..64 children whose centre is nearer to
+ * the query than `near` cell diagonals (d_T < near |B_T|, FP32; +inf: everywhere, 0: nowhere, which
+ * is the mass-proportional estimator); elsewhere the pick is by mass. Same random stream layout;
+ * opts->sampling must be 0. schedule 0 scores the children of a warp's gated decisions together on
+ * the tensor cores (mma.sync m16n8k16: FP16 features and activations, FP16 weights, FP32
+ * accumulation); schedule 1 is one thread per query with FP32 features and activations. */
 SBH_API sbh_status sbh_eval_learned(const sbh_tree* tree, const sbh_mlp* net, const float* queries, int64_t nq,
                                     sbh_kernel kernel, int32_t samples_per_subdomain, uint64_t seed,
-                                    const sbh_eval_opts* opts, float* out, void* stream);
+                                    const sbh_eval_opts* opts, float near, float* out, void* stream);
 SBH_API void sbh_mlp_free(sbh_mlp* net);
 
 /* Deterministic Barnes-Hut (Algorithm 1) on the 8-ary tree: a node is used whole when it is a

@@ -110,13 +110,15 @@ def load_library():
         lib.sbh_mlp_get_weights.argtypes = [P, P, P, P]
         lib.sbh_mlp_scores.argtypes = [P, P, i64, P, P]
         lib.sbh_mlp_loss_grad.argtypes = [P, P, P, P, i64, P, P, P]
-        lib.sbh_mlp_train.argtypes = [P, P, P, i64, _Kernel, i32, C.c_float, P, P]
-        lib.sbh_eval_learned.argtypes = [P, P, P, i64, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts), P, P]
+        lib.sbh_mlp_dataset.argtypes = [P, P, _Kernel, P, P, P, i64, P, P, P]
+        lib.sbh_mlp_train.argtypes = [P, P, P, i64, _Kernel, C.c_float, i32, C.c_float, P, P]
+        lib.sbh_eval_learned.argtypes = [P, P, P, i64, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts), C.c_float, P,
+                                         P]
         lib.sbh_mlp_free.argtypes = [P]
         lib.sbh_mlp_free.restype = None
         for f in ("sbh_build", "sbh_eval", "sbh_eval_count", "sbh_eval_grad", "sbh_eval_bh", "sbh_eval_brute",
                   "sbh_tree_info", "sbh_tree_export", "sbh_mlp_create", "sbh_mlp_set_weights",
-                  "sbh_mlp_get_weights", "sbh_mlp_scores", "sbh_mlp_loss_grad", "sbh_mlp_train",
+                  "sbh_mlp_get_weights", "sbh_mlp_scores", "sbh_mlp_loss_grad", "sbh_mlp_dataset", "sbh_mlp_train",
                   "sbh_eval_learned"):
             getattr(lib, f).restype = i32
         _lib = lib
@@ -515,23 +517,50 @@ def sbh_mlp_loss_grad(net: Mlp, feats, targets, offsets, stream=None):
     return loss, grad
 
 
-def sbh_mlp_train(net: Mlp, tree: Tree, queries, kernel="coulomb", steps: int = 200, lr: float = 3e-3,
-                  stream=None, softening: float = 1e-3, alpha: float = 200.0, affine=(0.0, 0.0, 0.0)):
-    """Fit the proposal to the tree's own child residuals at training queries [nq, 3]; returns the
-    loss before each step (numpy [steps])."""
+def _int_dev(t, name, dtype):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous {dtype} CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def sbh_mlp_dataset(tree: Tree, queries, set_query, set_node, set_offsets, kernel="coulomb", stream=None,
+                    softening: float = 1e-3, alpha: float = 200.0, affine=(0.0, 0.0, 0.0)):
+    """Features [rows, 6] and |exact child residual| targets [rows] of explicit decision sets
+    (node set_node[s] at query set_query[s], int32; rows set_offsets[s] .. set_offsets[s+1]-1, int64)."""
+    torch = _torch()
+    torch_i32, torch_i64 = torch.int32, torch.int64
+    n_sets = int(set_node.numel())
+    rows = int(set_offsets[-1].item()) if n_sets else 0
+    feats = torch.empty((rows, 6), dtype=torch.float32, device=queries.device)
+    targets = torch.empty(rows, dtype=torch.float32, device=queries.device)
+    k = _kernel_arg(kernel, softening, alpha, affine)
+    _check(load_library().sbh_mlp_dataset(tree.handle, _dev(queries, "queries", 3), k,
+                                          _int_dev(set_query, "set_query", torch_i32),
+                                          _int_dev(set_node, "set_node", torch_i32),
+                                          _int_dev(set_offsets, "set_offsets", torch_i64), n_sets,
+                                          _dev(feats, "feats", 6), _dev(targets, "targets"), _stream(stream)))
+    return feats, targets
+
+
+def sbh_mlp_train(net: Mlp, tree: Tree, queries, kernel="coulomb", near: float = float("inf"), steps: int = 200,
+                  lr: float = 3e-3, stream=None, softening: float = 1e-3, alpha: float = 200.0,
+                  affine=(0.0, 0.0, 0.0)):
+    """Fit the proposal to the residuals at the decisions the estimator's own paths reach from the
+    training queries [nq, 3]; returns the loss before each step (numpy [steps])."""
     import numpy as np
     losses = np.zeros(max(int(steps), 1), dtype=np.float32)
     k = _kernel_arg(kernel, softening, alpha, affine)
     _check(load_library().sbh_mlp_train(net.handle, tree.handle, _dev(queries, "queries", 3), int(queries.shape[0]),
-                                        k, int(steps), C.c_float(lr), losses.ctypes.data_as(C.c_void_p),
-                                        _stream(stream)))
+                                        k, C.c_float(near), int(steps), C.c_float(lr),
+                                        losses.ctypes.data_as(C.c_void_p), _stream(stream)))
     return losses[:int(steps)]
 
 
 def sbh_eval_learned(tree: Tree, net: Mlp, queries, kernel="coulomb", samples_per_subdomain: int = 1,
-                     seed: int = 0, opts: EvalOpts | None = None, out=None, stream=None, softening: float = 1e-3,
-                     alpha: float = 200.0, affine=(0.0, 0.0, 0.0)):
-    """Estimate with the learned child proposal; returns out [nq]."""
+                     seed: int = 0, opts: EvalOpts | None = None, near: float = float("inf"), out=None, stream=None,
+                     softening: float = 1e-3, alpha: float = 200.0, affine=(0.0, 0.0, 0.0)):
+    """Estimate with the learned child proposal at nodes nearer than `near` cell diagonals; returns out [nq]."""
     torch = _torch()
     nq = int(queries.shape[0])
     if out is None:
@@ -539,6 +568,6 @@ def sbh_eval_learned(tree: Tree, net: Mlp, queries, kernel="coulomb", samples_pe
     k = _kernel_arg(kernel, softening, alpha, affine)
     _check(load_library().sbh_eval_learned(tree.handle, net.handle, _dev(queries, "queries", 3), nq, k,
                                            int(samples_per_subdomain), C.c_uint64(int(seed) & (2**64 - 1)),
-                                           C.byref(opts) if opts is not None else None, _dev(out, "out"),
-                                           _stream(stream)))
+                                           C.byref(opts) if opts is not None else None, C.c_float(near),
+                                           _dev(out, "out"), _stream(stream)))
     return out

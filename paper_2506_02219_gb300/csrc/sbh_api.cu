@@ -440,12 +440,41 @@ sbh_status sbh_mlp_loss_grad(sbh_mlp* net, const float* feats, const float* targ
     return SBH_OK;
 }
 
+sbh_status sbh_mlp_dataset(const sbh_tree* tree, const float* queries, sbh_kernel kernel, const int32_t* set_query,
+                           const int32_t* set_node, const int64_t* set_offsets, int64_t n_sets, float* feats,
+                           float* targets, void* stream)
+{
+    g_err[0] = 0;
+    if (!tree || !tree->t4.built) return fail(SBH_EINVAL, "tree missing");
+    if (n_sets < 0) return fail(SBH_EINVAL, "n_sets < 0");
+    sbh::KernelParams kp;
+    sbh_status st = check_kernel(kernel, &kp);
+    if (st != SBH_OK) return st;
+    if (kernel.kind == SBH_WINDING && !tree->has_normals)
+        return fail(SBH_EINVAL, "the winding-number kernel needs a tree built with normals");
+    if (n_sets == 0) return SBH_OK;
+    if (!device_ptr(queries) || !device_ptr(set_query) || !device_ptr(set_node) || !device_ptr(set_offsets) ||
+        !device_ptr(feats) || !device_ptr(targets))
+        return fail(SBH_EINVAL, "all buffers must be device memory");
+    cudaError_t e = sbh::mlp_dataset(tree, queries, set_query, set_node, n_sets, set_offsets, kp, feats, targets,
+                                     (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_mlp_dataset");
+    return SBH_OK;
+}
+
+namespace {
+constexpr int kTrainPaths = 4;            // paths per subdomain walked by each training query
+constexpr int kTrainSetsPerQuery = 4096;  // cap on the decision sets one training query contributes
+constexpr uint64_t kTrainSeed = 0x7EA1ull;
+}  // namespace
+
 sbh_status sbh_mlp_train(sbh_mlp* net, const sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel,
-                         int32_t steps, float lr, float* losses, void* stream)
+                         float near, int32_t steps, float lr, float* losses, void* stream)
 {
     g_err[0] = 0;
     if (!net || !tree || !tree->t4.built) return fail(SBH_EINVAL, "net or tree missing");
     if (nq < 1 || nq > (1 << 20) || steps < 0 || !(lr > 0.0f)) return fail(SBH_EINVAL, "need 1 <= nq <= 2^20, steps >= 0, lr > 0");
+    if (!(near >= 0.0f)) return fail(SBH_EINVAL, "near must be >= 0");
     sbh::KernelParams kp;
     sbh_status st = check_kernel(kernel, &kp);
     if (st != SBH_OK) return st;
@@ -453,61 +482,84 @@ sbh_status sbh_mlp_train(sbh_mlp* net, const sbh_tree* tree, const float* querie
         return fail(SBH_EINVAL, "the winding-number kernel needs a tree built with normals");
     if (!device_ptr(queries)) return fail(SBH_EINVAL, "queries must be device memory");
     cudaStream_t s = (cudaStream_t)stream;
-    // decision sets: the subdomains with 2..64 children
-    const sbh::TreeCtrl& c = tree->host_ctrl4;
-    std::vector<uint32_t> meta(c.n_sub);
-    cudaError_t e = cudaMemcpyAsync(meta.data(), tree->t4.meta + c.first_sub, c.n_sub * sizeof(uint32_t),
-                                    cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e, "sbh_mlp_train");
-    std::vector<int32_t> nodes;
-    std::vector<int32_t> nch;
-    for (int32_t i = 0; i < c.n_sub; ++i) {
-        const uint32_t nc = sbh::meta_nchild(meta[i]);
-        if (nc >= 2 && nc <= 64) { nodes.push_back(c.first_sub + i); nch.push_back((int32_t)nc); }
-    }
-    if (nodes.empty()) return fail(SBH_EUNSUPPORTED, "the tree has no subdomain with 2..64 children to learn from");
-    const int64_t n_sets = nq * (int64_t)nodes.size();
-    std::vector<int64_t> off((size_t)n_sets + 1);
-    off[0] = 0;
-    for (int64_t j = 0, k = 0; j < nq; ++j)
-        for (size_t a = 0; a < nodes.size(); ++a, ++k) off[(size_t)k + 1] = off[(size_t)k] + nch[a];
-    const int64_t rows = off[(size_t)n_sets];
-    if (rows > (int64_t(1) << 26)) return fail(SBH_EINVAL, "training set too large: nq x (children of the subdomains) > 2^26");
+    const sbh::TreeView T = tree->t4.view();
+    // 1. the decision sets the estimator's own paths reach (count, offsets, fill)
+    int32_t* dcount = nullptr;
+    int64_t* dbase = nullptr;
+    int32_t *set_q = nullptr, *set_node = nullptr;
+    int64_t *rows = nullptr, *doff = nullptr;
     float *feats = nullptr, *targets = nullptr;
-    int64_t* doff = nullptr;
-    int32_t* dnodes = nullptr;
-    e = sbh::dalloc((void**)&feats, rows * 6 * sizeof(float), s);
-    if (e == cudaSuccess) e = sbh::dalloc((void**)&targets, rows * sizeof(float), s);
-    if (e == cudaSuccess) e = sbh::dalloc((void**)&doff, off.size() * sizeof(int64_t), s);
-    if (e == cudaSuccess) e = sbh::dalloc((void**)&dnodes, nodes.size() * sizeof(int32_t), s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(doff, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(dnodes, nodes.data(), nodes.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess)
-        e = sbh::mlp_dataset(tree, queries, (int)nq, dnodes, (int)nodes.size(), doff, kp, feats, targets, s);
-    for (int32_t k = 0; k < steps && e == cudaSuccess; ++k) {
-        e = sbh::mlp_loss_grad(net->M, feats, targets, doff, n_sets, s);
-        if (e == cudaSuccess && losses) e = cudaMemcpyAsync(&losses[k], net->M.loss, sizeof(float), cudaMemcpyDeviceToHost, s);
-        if (e == cudaSuccess) e = sbh::mlp_adam_step(net->M, lr, s);
+    std::vector<int32_t> count((size_t)nq);
+    std::vector<int64_t> base((size_t)nq);
+    cudaError_t e = sbh::dalloc((void**)&dcount, nq * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = sbh::mlp_visit(T, queries, (int)nq, kTrainPaths, kTrainSeed, near, kTrainSetsPerQuery,
+                                             dcount, nullptr, nullptr, nullptr, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(count.data(), dcount, nq * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int64_t n_sets = 0;
+    for (int64_t j = 0; j < nq; ++j) { base[(size_t)j] = n_sets; n_sets += count[(size_t)j]; }
+    std::vector<int64_t> off;
+    if (e == cudaSuccess && n_sets == 0) {
+        sbh::dfree(dcount, s);
+        return fail(SBH_EUNSUPPORTED, "no decision set within reach of the training queries (raise near)");
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host copies of `losses` (pageable) are complete
+    if (e == cudaSuccess) e = sbh::dalloc((void**)&dbase, nq * sizeof(int64_t), s);
+    if (e == cudaSuccess) e = sbh::dalloc((void**)&set_q, n_sets * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = sbh::dalloc((void**)&set_node, n_sets * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = sbh::dalloc((void**)&rows, (n_sets + 1) * sizeof(int64_t), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dbase, base.data(), nq * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = sbh::mlp_visit(T, queries, (int)nq, kTrainPaths, kTrainSeed, near, kTrainSetsPerQuery,
+                                             nullptr, dbase, set_q, set_node, s);
+    if (e == cudaSuccess) e = sbh::mlp_set_rows(T, set_node, n_sets, rows, s);
+    if (e == cudaSuccess) {
+        off.resize((size_t)n_sets + 1);
+        e = cudaMemcpyAsync(off.data() + 1, rows, n_sets * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int64_t total = 0;
+    if (e == cudaSuccess) {
+        off[0] = 0;
+        for (int64_t i = 1; i <= n_sets; ++i) off[(size_t)i] += off[(size_t)i - 1];
+        total = off[(size_t)n_sets];
+    }
+    bool too_large = e == cudaSuccess && total > (int64_t(1) << 26);
+    // 2. features and |exact child residual| targets
+    if (e == cudaSuccess && !too_large) {
+        doff = rows;  // reuse: n_sets + 1 entries
+        e = cudaMemcpyAsync(doff, off.data(), (n_sets + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = sbh::dalloc((void**)&feats, total * 6 * sizeof(float), s);
+        if (e == cudaSuccess) e = sbh::dalloc((void**)&targets, total * sizeof(float), s);
+        if (e == cudaSuccess) e = sbh::mlp_dataset(tree, queries, set_q, set_node, n_sets, doff, kp, feats, targets, s);
+        // 3. full-batch Adam steps
+        for (int32_t k = 0; k < steps && e == cudaSuccess; ++k) {
+            e = sbh::mlp_loss_grad(net->M, feats, targets, doff, n_sets, s);
+            if (e == cudaSuccess && losses)
+                e = cudaMemcpyAsync(&losses[k], net->M.loss, sizeof(float), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = sbh::mlp_adam_step(net->M, lr, s);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host copies of `losses` are complete
+    }
+    sbh::dfree(dcount, s);
+    sbh::dfree(dbase, s);
+    sbh::dfree(set_q, s);
+    sbh::dfree(set_node, s);
+    sbh::dfree(rows, s);
     sbh::dfree(feats, s);
     sbh::dfree(targets, s);
-    sbh::dfree(doff, s);
-    sbh::dfree(dnodes, s);
     if (e != cudaSuccess) return cuda_fail(e, "sbh_mlp_train");
+    if (too_large) return fail(SBH_EINVAL, "training set too large (more than 2^26 rows): use fewer training queries");
     return SBH_OK;
 }
 
 sbh_status sbh_eval_learned(const sbh_tree* tree, const sbh_mlp* net, const float* queries, int64_t nq,
                             sbh_kernel kernel, int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
-                            float* out, void* stream)
+                            float near, float* out, void* stream)
 {
     g_err[0] = 0;
     if (!tree || !tree->t4.built || !net) return fail(SBH_EINVAL, "tree or net missing");
     if (nq < 0) return fail(SBH_EINVAL, "nq < 0");
     if (samples_per_subdomain < 1) return fail(SBH_EINVAL, "samples_per_subdomain must be >= 1");
+    if (!(near >= 0.0f)) return fail(SBH_EINVAL, "near must be >= 0");
     sbh::KernelParams kp;
     sbh_status st = check_kernel(kernel, &kp);
     if (st != SBH_OK) return st;
@@ -516,10 +568,11 @@ sbh_status sbh_eval_learned(const sbh_tree* tree, const sbh_mlp* net, const floa
     sbh_eval_opts o = {0, 0, 0, 0, 0};
     if (opts) o = *opts;
     if (!opts_ok(o)) return fail(SBH_EINVAL, "sbh_eval_opts out of range");
+    if (o.sampling != 0) return fail(SBH_EINVAL, "the learned proposal replaces the path-index sampling: sampling must be 0");
     if (nq == 0) return SBH_OK;
     if (!device_ptr(queries) || !device_ptr(out)) return fail(SBH_EINVAL, "queries and out must be device memory");
-    cudaError_t e = sbh::launch_stoch_learned(tree->t4.view(), net->M.wh, queries, nq, kp, samples_per_subdomain, seed,
-                                              o, out, (cudaStream_t)stream);
+    cudaError_t e = sbh::launch_stoch_learned(tree->t4.view(), tree->host_ctrl4, net->M.wh, near, queries, nq, kp,
+                                              samples_per_subdomain, seed, o, out, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "sbh_eval_learned launch");
     return SBH_OK;
 }

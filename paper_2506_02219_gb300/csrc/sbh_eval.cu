@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                                                     KernelParams kp, int S, uint2 key, int sampling, int rr,
                                                     int coherent, int raw_sum, float* __restrict__ out,
                                                     float* __restrict__ grad, unsigned long long* __restrict__ counts,
-                                                    const __half* __restrict__ mlpw)
+                                                    const __half* __restrict__ mlpw, float near)
 {
     constexpr bool COUNT = MODE == kModeCount;
     constexpr bool GRAD = MODE == kModeGrad;
@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                     int pick = 0;
                     float pick_prob = 1.0f;
                     if (LEARNED) {
-                        pick = learned_pick(T, sw, sdiam, node, mT, pT, q, KIND == SBH_WINDING, x.x, &pick_prob);
+                        pick = learned_pick(T, sw, sdiam, node, mT, pT, dT, near, q, KIND == SBH_WINDING, x.x,
+                                            &pick_prob);
                     } else if (sampling == 0) {
                         const float u = unit24(x.x);
                         for (int k = 0; k < nc - 1; ++k) pick += (__ldg(&T.cdf[f + k]) <= u) ? 1 : 0;
@@ -222,7 +223,8 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
 template <int MODE>
 cudaError_t launch_lane_impl(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
                              uint64_t seed, const sbh_eval_opts& o, float* out, float* grad,
-                             unsigned long long* counts, cudaStream_t s, const __half* mlpw = nullptr)
+                             unsigned long long* counts, cudaStream_t s, const __half* mlpw = nullptr,
+                             float near = 0.0f)
 {
     if (nq <= 0) return cudaSuccess;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -232,16 +234,16 @@ cudaError_t launch_lane_impl(const TreeView& T, const float* Q, int64_t nq, cons
     const unsigned b = (unsigned)blocks;
     switch (kp.kind) {
     case SBH_COULOMB:
-        k_stoch_eval<SBH_COULOMB, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw);
+        k_stoch_eval<SBH_COULOMB, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw, near);
         break;
     case SBH_WINDING:
-        k_stoch_eval<SBH_WINDING, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw);
+        k_stoch_eval<SBH_WINDING, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw, near);
         break;
     case SBH_SMOOTHDIST:
-        k_stoch_eval<SBH_SMOOTHDIST, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw);
+        k_stoch_eval<SBH_SMOOTHDIST, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw, near);
         break;
     case SBH_AFFINE:
-        k_stoch_eval<SBH_AFFINE, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw);
+        k_stoch_eval<SBH_AFFINE, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw, near);
         break;
     default:
         return cudaErrorInvalidValue;
@@ -266,12 +268,14 @@ cudaError_t launch_stoch_lane(const TreeView& T, const float* Q, int64_t nq, con
     return launch_lane_impl<kModeEval>(T, Q, nq, kp, S, seed, o, out, nullptr, nullptr, s);
 }
 
-cudaError_t launch_stoch_learned(const TreeView& T, const void* mlp_half, const float* Q, int64_t nq,
-                                 const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
-                                 cudaStream_t s)
+cudaError_t launch_stoch_learned(const TreeView& T, const TreeCtrl& host_ctrl, const void* mlp_half, float near,
+                                 const float* Q, int64_t nq, const KernelParams& kp, int S, uint64_t seed,
+                                 const sbh_eval_opts& o, float* out, cudaStream_t s)
 {
-    return launch_lane_impl<kModeLearned>(T, Q, nq, kp, S, seed, o, out, nullptr, nullptr, s,
-                                          (const __half*)mlp_half);
+    if (o.schedule == 1)
+        return launch_lane_impl<kModeLearned>(T, Q, nq, kp, S, seed, o, out, nullptr, nullptr, s,
+                                              (const __half*)mlp_half, near);
+    return launch_stoch_batched_learned(T, host_ctrl, mlp_half, near, Q, nq, kp, S, seed, o, out, s);
 }
 
 cudaError_t launch_stoch_count(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,

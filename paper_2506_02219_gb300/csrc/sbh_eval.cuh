@@ -27,10 +27,14 @@ void multi_fill_desc(void* dst, const TreeView& T, const float* Q, float* out, i
 cudaError_t launch_stoch_lane(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
                               uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s);
 
-// the estimator with the learned child proposal (mlp_half: device FP16 weights)
-cudaError_t launch_stoch_learned(const TreeView& T, const void* mlp_half, const float* Q, int64_t nq,
-                                 const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
-                                 cudaStream_t s);
+// the estimator with the learned child proposal (mlp_half: device FP16 weights; the network is
+// used at nodes nearer to the query than `near` cell diagonals); schedule 1 = one thread per query
+cudaError_t launch_stoch_learned(const TreeView& T, const TreeCtrl& host_ctrl, const void* mlp_half, float near,
+                                 const float* Q, int64_t nq, const KernelParams& kp, int S, uint64_t seed,
+                                 const sbh_eval_opts& o, float* out, cudaStream_t s);
+cudaError_t launch_stoch_batched_learned(const TreeView& T, const TreeCtrl& host_ctrl, const void* mlp_half,
+                                         float near, const float* Q, int64_t nq, const KernelParams& kp, int S,
+                                         uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s);
 
 cudaError_t launch_stoch_count(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
                                uint64_t seed, const sbh_eval_opts& o, unsigned long long* counts, cudaStream_t s);

@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include "sbh_eval.cuh"
+#include "sbh_learned.cuh"
 
 namespace sbh {
 
@@ -127,6 +128,25 @@ __device__ __forceinline__ int pick_child(const TreeView& T, const Stage& S, int
     return lo - 1;
 }
 
+// per-warp scratch of the learned pick: one chunk of FP16 feature rows, the rows of one group of
+// decisions (exp of the clamped score, child mass), and the gated decisions of the batch
+constexpr int kLearnRows = 256;
+struct __align__(16) LearnScratch {
+    uint32_t A[32 * kChunkWords];
+    float sc[32];
+    float pe[kLearnRows];   // within each decision: prefix sums of exp(clamped score)
+    float pm[kLearnRows];   //                       prefix sums of the child masses
+    uint8_t rk[kLearnRows]; // decision (compact index) of each row
+    float qx[32], qy[32], qz[32];
+    float lnBT[32], lnmT[32], lndT[32];  // logs of the node's cell diagonal, mass, guarded distance
+    float u[32];            // the decision's uniform draw
+    float prob[32];         // out: probability of the child picked
+    int32_t f[32];
+    int32_t off[32];
+    int32_t nc[32];
+    int32_t pick[32];       // out: child picked (0-based)
+};
+
 struct Params {
     TreeView T;
     const float* Q;
@@ -136,11 +156,147 @@ struct Params {
     uint2 key;
     int sampling, rr, coherent, raw_sum;
     float* out;
+    // learned proposal only
+    const __half* mlpw;
+    float near;
+    const MlpFrag* frag;     // shared memory, set in the kernel
+    LearnScratch* learn;     // shared memory, one per warp, set in the kernel
 };
+
+// The learned picks of the gated lanes of a decision batch (every lane of the warp takes part).
+// Rows = the children of the gated decisions in lane order, processed in groups of whole
+// decisions of at most kLearnRows rows, 32 rows (one per lane) at a time: features, tensor-core
+// scores, and segmented prefix sums (restarting at each decision's first row) of exp(score) and
+// of the child masses. Then each row tests whether its decision's draw u falls in its interval
+// [cum_{r-1}, cum_r) of the mixed proposal's cumulative distribution
+//   cum_r = (1 - eps) Pe_r / Z + eps Pm_r / M   (Z, M: the decision's totals),
+// the last row taking [cum_{r-1}, 1): exactly one row of each decision is picked, and its
+// probability is the width of its interval.
+template <int KIND>
+__device__ __noinline__ void learned_picks(const Params& P, const Stage& S, const float* sdiam, unsigned gm,
+                                           bool gated, float3 q, float4 pT, float BT, int32_t f, int nc, float u,
+                                           int32_t& child, float& prob)
+{
+    const float* slnB = sdiam + kDiamLevels;  // ln |B| per level, stored after the diagonals
+    const TreeView& T = P.T;
+    LearnScratch& L = P.learn[threadIdx.x >> 5];
+    const uint32_t lane = lane_id();
+    const int k = __popc(gm & lanemask_lt());
+    const int v = gated ? nc : 0;
+    int incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if ((int)lane >= o) incl += y;
+    }
+    const int off = incl - v;
+    if (gated) {
+        const float tx = pT.x - q.x, ty = pT.y - q.y, tz = pT.z - q.z;
+        const float t2 = tx * tx + ty * ty + tz * tz;
+        L.qx[k] = q.x; L.qy[k] = q.y; L.qz[k] = q.z;
+        L.f[k] = f; L.off[k] = off; L.nc[k] = nc; L.u[k] = u;
+        L.lnBT[k] = __logf(BT);
+        L.lnmT[k] = __logf(pT.w);
+        L.lndT[k] = __logf((t2 > 0.0f ? t2 * rsqrtf(t2) : 0.0f) + 1e-6f * BT);
+    }
+    const int G = __popc(gm);
+    MlpRegs Wr;
+    load_mlp_regs(*P.frag, Wr);
+    __syncwarp();
+    for (int base_k = 0; base_k < G;) {
+        const int off_base = L.off[base_k];
+        const bool member = gated && k >= base_k && off + nc - off_base <= kLearnRows;
+        const int end_k = base_k + __popc(__ballot_sync(0xFFFFFFFFu, member));
+        const int R = L.off[end_k - 1] + L.nc[end_k - 1] - off_base;
+        float carry_e = 0.0f, carry_m = 0.0f;  // the open segment's sums at the end of the last chunk
+        for (int r0 = 0; r0 < R; r0 += 32) {
+            const int r = r0 + (int)lane;
+            const bool live = r < R;
+            float x[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            float mc = 0.0f;
+            bool head = false;
+            if (live) {
+                int lo = base_k, hi = end_k - 1;  // the decision that owns row r
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (L.off[mid] - off_base <= r) lo = mid;
+                    else hi = mid - 1;
+                }
+                L.rk[r] = (uint8_t)lo;
+                const int c = off_base + r - L.off[lo];
+                head = c == 0;
+                const int32_t ch = L.f[lo] + c;
+                const float4 pc = ld_pm(T, S, ch);
+                const uint32_t lc = meta_level(ld_meta(T, S, ch));
+                // the features of features_of, with fast logarithms and the node's logs shared
+                const float vx = pc.x - L.qx[lo], vy = pc.y - L.qy[lo], vz = pc.z - L.qz[lo];
+                const float v2 = vx * vx + vy * vy + vz * vz;
+                const float Bc = sdiam[lc], lnBc = slnB[lc];
+                const float dc = (v2 > 0.0f ? v2 * rsqrtf(v2) : 0.0f) + 1e-6f * Bc;
+                const float lndc = __logf(dc);
+                x[0] = lndc - lnBc;
+                x[1] = __logf(pc.w) - L.lnmT[lo];
+                x[2] = lnBc - L.lnBT[lo];
+                x[3] = lndc - L.lndT[lo];
+                if constexpr (KIND == SBH_WINDING) {
+                    const float4 N = ld_dip(T, S, ch);
+                    const float n2 = N.x * N.x + N.y * N.y + N.z * N.z;
+                    const float inv_n = n2 > 0.0f ? rsqrtf(n2) : 0.0f;
+                    x[4] = __fdividef(n2 * inv_n, pc.w);
+                    x[5] = __fdividef((vx * N.x + vy * N.y + vz * N.z) * inv_n, dc);
+                }
+                mc = pc.w;
+            }
+            store_feature_row(&L.A[lane * kChunkWords], x, live);
+            __syncwarp();
+            const float sco = score_chunk(Wr, L.A, L.sc);
+            // segmented inclusive prefix sums over the lanes, restarting at each decision's head
+            float pe = live ? __expf(clamp_score(sco)) : 0.0f, pm = mc;
+            const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
+            const unsigned at_or_below = heads & (0xFFFFFFFFu >> (31u - lane));
+            const int start = at_or_below ? 31 - __clz(at_or_below) : -1;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float ye = __shfl_up_sync(0xFFFFFFFFu, pe, o);
+                const float ym = __shfl_up_sync(0xFFFFFFFFu, pm, o);
+                if ((int)lane - o >= start && (int)lane >= o) { pe += ye; pm += ym; }
+            }
+            if (start < 0) { pe += carry_e; pm += carry_m; }  // the segment began in an earlier chunk
+            if (live) { L.pe[r] = pe; L.pm[r] = pm; }
+            carry_e = __shfl_sync(0xFFFFFFFFu, pe, 31);
+            carry_m = __shfl_sync(0xFFFFFFFFu, pm, 31);
+        }
+        __syncwarp();
+        for (int r0 = 0; r0 < R; r0 += 32) {
+            const int r = r0 + (int)lane;
+            if (r < R) {
+                const int kd = L.rk[r];
+                const int first = L.off[kd] - off_base, last = first + L.nc[kd] - 1;
+                const float a = (1.0f - kMixEps) / L.pe[last], b = kMixEps / L.pm[last];
+                const float hi = fmaf(L.pe[r], a, L.pm[r] * b);
+                const float lo = r == first ? 0.0f : fmaf(L.pe[r - 1], a, L.pm[r - 1] * b);
+                const float ud = L.u[kd];
+                if (ud >= lo && (ud < hi || r == last)) {
+                    L.pick[kd] = r - first;
+                    L.prob[kd] = r == last ? 1.0f - lo : hi - lo;
+                }
+            }
+        }
+        __syncwarp();
+        if (member) {
+            child = f + L.pick[k];
+            prob = L.prob[k];
+        }
+        __syncwarp();
+        base_k = end_k;
+    }
+}
 
 // One decision per lane (Algorithm 2's loop body up to the break test). On a continue the lane
 // appends a swap task for its node and a decision task for the chosen child.
-template <int KIND>
+// With the learned proposal, wT carries p(path reaches node) (the product of the picks'
+// probabilities) and wa = 1, so that p_agg = wT / wa in both cases.
+template <int KIND, bool LEARNED>
 __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpState& W, const float* sdiam, bool valid,
                                        int32_t node,
                                        uint32_t tag, int32_t ai, float prr, float dT, float wT, float wa,
@@ -151,14 +307,34 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
     int32_t child = 0;
     float dc = 0.0f, wc = 0.0f, w = 0.0f, prr2 = 0.0f;
     const uint32_t slot = tag & 31u;
+    const uint32_t depth = (tag >> 5) & 0xFFu;
+    float3 q = make_float3(0.0f, 0.0f, 0.0f);
+    uint4 x = make_uint4(0u, 0u, 0u, 0u);
+    uint32_t mT = 0;
+    int32_t f = 0;
+    int nc = 0;
     if (valid) {
-        const uint32_t depth = (tag >> 5) & 0xFFu, s = tag >> 13;
-        const float3 q = make_float3(W.qx[slot], W.qy[slot], W.qz[slot]);
-        const uint4 x = philox4x32_10(make_uint4(W.qctr[slot], (uint32_t)ai, s, depth), P.key);
-        const uint32_t mT = ld_meta(T, S, node);
-        const int32_t f = ld_fc(T, S, node);
-        const int nc = (int)meta_nchild(mT);
-        child = f + pick_child(T, S, node, f, nc, x.x, P.sampling);
+        q = make_float3(W.qx[slot], W.qy[slot], W.qz[slot]);
+        x = philox4x32_10(make_uint4(W.qctr[slot], (uint32_t)ai, tag >> 13, depth), P.key);
+        mT = ld_meta(T, S, node);
+        f = ld_fc(T, S, node);
+        nc = (int)meta_nchild(mT);
+    }
+    float pick_prob = 1.0f;
+    if constexpr (LEARNED) {
+        const float4 pT = valid ? ld_pm(T, S, node) : make_float4(0.0f, 0.0f, 0.0f, 1.0f);
+        const float BT = sdiam[meta_level(mT)];
+        const bool gated = valid && learned_gate(nc, dT, P.near, BT);
+        const unsigned gm = __ballot_sync(0xFFFFFFFFu, gated);
+        if (valid && !gated) {
+            child = f + pick_child(T, S, node, f, nc, x.x, 0);
+            pick_prob = ld_pm(T, S, child).w / pT.w;
+        }
+        if (gm) learned_picks<KIND>(P, S, sdiam, gm, gated, q, pT, BT, f, nc, unit24(x.x), child, pick_prob);
+    } else {
+        if (valid) child = f + pick_child(T, S, node, f, nc, x.x, P.sampling);
+    }
+    if (valid) {
         const float4 pc = ld_pm(T, S, child);
         const uint32_t mc = ld_meta(T, S, child);
         dc = dist_rn(pc.x, pc.y, pc.z, q);
@@ -170,7 +346,8 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
             prr2 = prr * p;
             const float pagg = wT / wa;
             w = 1.0f / (pagg * prr2) / (float)P.S;
-            wc = P.sampling ? (float)(__ldg(&T.ne[child]) - __ldg(&T.nb[child])) : pc.w;
+            if constexpr (LEARNED) wc = wT * pick_prob;
+            else wc = P.sampling ? (float)(__ldg(&T.ne[child]) - __ldg(&T.nb[child])) : pc.w;
             // a path that reaches a source point stops there: no decision task for it (levels
             // strictly increase, so depth < kMaxDepth always holds; the test only guards a damaged tree)
             if (meta_kind(mc) == kPoint || depth + 1 >= (uint32_t)kMaxDepth) wc = -1.0f;
@@ -200,7 +377,7 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
 }
 
 // Run up to 32 decision tasks from the front of the ring.
-template <int KIND>
+template <int KIND, bool LEARNED>
 __device__ __forceinline__ void decision_batch(const Params& P, const Stage& S, WarpState& W, const float* sdiam,
                                                uint32_t& d_head,
                                                uint32_t& d_tail, uint32_t& s_tail)
@@ -218,7 +395,7 @@ __device__ __forceinline__ void decision_batch(const Params& P, const Stage& S, 
     }
     __syncwarp();  // every task is read before new ones may reuse its slot
     d_head += take;
-    decide<KIND>(P, S, W, sdiam, valid, node, tag, ai, prr, dT, wT, wa, d_tail, s_tail);
+    decide<KIND, LEARNED>(P, S, W, sdiam, valid, node, tag, ai, prr, dT, wT, wa, d_tail, s_tail);
 }
 
 // Run up to 32 swap tasks: w * (sum_children m_c f(p_c, q) - m_T f(p_T, q)), added to the
@@ -304,7 +481,7 @@ __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, Warp
 
 // One tile of 32 queries (query index tile * 32 + lane within the set described by P), run by
 // one warp: control variates and depth-0 decisions lane-parallel, everything else as tasks.
-template <int KIND>
+template <int KIND, bool LEARNED>
 __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpState& W, const float* sdiam,
                                          int64_t tile)
 {
@@ -340,13 +517,14 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
             }
         }
         if (meta_kind(ma) == kPoint) continue;
-        const float wa = P.sampling ? (float)(__ldg(&T.ne[a]) - __ldg(&T.nb[a])) : pa.w;
+        const float wa = LEARNED ? 1.0f : (P.sampling ? (float)(__ldg(&T.ne[a]) - __ldg(&T.nb[a])) : pa.w);
         const float da = dist_rn(pa.x, pa.y, pa.z, q);
         for (int s = 0; s < P.S; ++s) {
-            decide<KIND>(P, S, W, sdiam, active, a, lane | ((uint32_t)s << 13), ai, 1.0f, da, wa, wa, d_tail, s_tail);
+            decide<KIND, LEARNED>(P, S, W, sdiam, active, a, lane | ((uint32_t)s << 13), ai, 1.0f, da, wa, wa, d_tail,
+                                  s_tail);
             while (s_tail - s_head >= 32u) swap_batch<KIND>(P, S, W, s_head, s_tail);
             while (d_tail - d_head >= 32u) {
-                decision_batch<KIND>(P, S, W, sdiam, d_head, d_tail, s_tail);
+                decision_batch<KIND, LEARNED>(P, S, W, sdiam, d_head, d_tail, s_tail);
                 while (s_tail - s_head >= 32u) swap_batch<KIND>(P, S, W, s_head, s_tail);
             }
         }
@@ -354,7 +532,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
     // drain the partial batches
     while (d_tail != d_head || s_tail != s_head) {
         if (s_tail != s_head) swap_batch<KIND>(P, S, W, s_head, s_tail);
-        if (d_tail != d_head) decision_batch<KIND>(P, S, W, sdiam, d_head, d_tail, s_tail);
+        if (d_tail != d_head) decision_batch<KIND, LEARNED>(P, S, W, sdiam, d_head, d_tail, s_tail);
     }
     __syncwarp();
     if (active) {
@@ -373,12 +551,28 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
     __syncwarp();
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_stoch_batched(Params P, int32_t stage_lo, uint32_t stage_n)
+// dynamic shared memory: [learned proposal: MlpFrag, one LearnScratch per warp] then the stage
+template <bool LEARNED>
+constexpr size_t learned_smem_bytes()
+{
+    return LEARNED ? sizeof(MlpFrag) + kWarpsPerBlock * sizeof(LearnScratch) : 0;
+}
+
+template <int KIND, bool LEARNED>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, LEARNED ? 2 : 3)
+    k_stoch_batched(Params P, int32_t stage_lo, uint32_t stage_n)
 {
     __shared__ WarpState s_state[kWarpsPerBlock];
-    __shared__ float sdiam[kDiamLevels];
-    extern __shared__ float4 s_stage[];
+    __shared__ float sdiam[LEARNED ? 2 * kDiamLevels : kDiamLevels];  // learned: then ln of each
+    extern __shared__ float4 s_dyn[];
+    float4* s_stage = s_dyn;
+    if constexpr (LEARNED) {
+        MlpFrag* F = reinterpret_cast<MlpFrag*>(s_dyn);
+        mlp_frag_fill(P.mlpw, *F);
+        P.frag = F;
+        P.learn = reinterpret_cast<LearnScratch*>(reinterpret_cast<unsigned char*>(s_dyn) + sizeof(MlpFrag));
+        s_stage = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_dyn) + learned_smem_bytes<LEARNED>());
+    }
     Stage S;
     S.lo = stage_lo;
     S.n = stage_n;
@@ -395,13 +589,16 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_stoch_batched(Params
         S.meta[i] = __ldg(&P.T.meta[v]);
         S.fc[i] = __ldg(&P.T.fc[v]);
     }
-    if (threadIdx.x < kDiamLevels) sdiam[threadIdx.x] = P.T.ctrl->diam[threadIdx.x];
+    if (threadIdx.x < kDiamLevels) {
+        sdiam[threadIdx.x] = P.T.ctrl->diam[threadIdx.x];
+        if (LEARNED) sdiam[kDiamLevels + threadIdx.x] = __logf(P.T.ctrl->diam[threadIdx.x]);
+    }
     __syncthreads();
     WarpState& W = s_state[threadIdx.x >> 5];
     const int64_t n_tiles = (P.nq + 31) / 32;
     const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t warp_stride = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t tile = warp_global; tile < n_tiles; tile += warp_stride) run_tile<KIND>(P, S, W, sdiam, tile);
+    for (int64_t tile = warp_global; tile < n_tiles; tile += warp_stride) run_tile<KIND, LEARNED>(P, S, W, sdiam, tile);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -458,18 +655,54 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_stoch_multi(MultiPar
             if (lane < (uint32_t)kDiamLevels) sdiam[lane] = D.T.ctrl->diam[lane];
             __syncwarp();
         }
-        run_tile<KIND>(P, S, W, sdiam, tile - M.sets[lo].tile_begin);
+        run_tile<KIND, false>(P, S, W, sdiam, tile - M.sets[lo].tile_begin);
     }
 }
 
-template <int KIND>
+template <int KIND, bool LEARNED>
 static cudaError_t launch_kind(const Params& P, unsigned blocks, int32_t lo, uint32_t n, cudaStream_t s)
 {
-    const size_t bytes = (size_t)n * (sizeof(float4) * (KIND == SBH_WINDING ? 2 : 1) + 3 * sizeof(uint32_t));
-    cudaError_t e = cudaFuncSetAttribute(k_stoch_batched<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    const size_t bytes = learned_smem_bytes<LEARNED>() +
+                         (size_t)n * (sizeof(float4) * (KIND == SBH_WINDING ? 2 : 1) + 3 * sizeof(uint32_t));
+    cudaError_t e = cudaFuncSetAttribute(k_stoch_batched<KIND, LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
     if (e != cudaSuccess) return e;
-    k_stoch_batched<KIND><<<blocks, 32 * kWarpsPerBlock, bytes, s>>>(P, lo, n);
+    k_stoch_batched<KIND, LEARNED><<<blocks, 32 * kWarpsPerBlock, bytes, s>>>(P, lo, n);
     return cudaSuccess;
+}
+
+template <bool LEARNED>
+static cudaError_t launch_batched_impl(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
+                                       const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o,
+                                       float* out, const void* mlp_half, float near, cudaStream_t s)
+{
+    if (nq <= 0) return cudaSuccess;
+    Params P;
+    P.T = T; P.Q = Q; P.nq = nq; P.kp = kp; P.S = S;
+    P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    P.sampling = o.sampling; P.rr = o.rr; P.coherent = o.seed_mode; P.raw_sum = o.raw_sum; P.out = out;
+    P.mlpw = (const __half*)mlp_half; P.near = near; P.frag = nullptr; P.learn = nullptr;
+    const int64_t tiles = (nq + 31) / 32;
+    int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    // stage generations 1 and 2 (the subdomains and their children), at most kStageMax nodes
+    // (half as many with the learned proposal, whose scratch takes the rest of the room)
+    const int32_t lo = host_ctrl.max_depth >= 1 ? host_ctrl.depth_base[1] : 0;
+    const int32_t hi = host_ctrl.depth_base[host_ctrl.max_depth >= 2 ? 3 : (host_ctrl.max_depth >= 1 ? 2 : 1)];
+    uint32_t n = (uint32_t)(hi > lo ? hi - lo : 0);
+    const uint32_t cap = LEARNED ? kStageMax / 2 : kStageMax;
+    if (n > cap) n = cap;
+    cudaError_t e;
+    switch (kp.kind) {
+    case SBH_COULOMB: e = launch_kind<SBH_COULOMB, LEARNED>(P, (unsigned)blocks, lo, n, s); break;
+    case SBH_WINDING: e = launch_kind<SBH_WINDING, LEARNED>(P, (unsigned)blocks, lo, n, s); break;
+    case SBH_SMOOTHDIST: e = launch_kind<SBH_SMOOTHDIST, LEARNED>(P, (unsigned)blocks, lo, n, s); break;
+    case SBH_AFFINE: e = launch_kind<SBH_AFFINE, LEARNED>(P, (unsigned)blocks, lo, n, s); break;
+    default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    note_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -478,30 +711,14 @@ cudaError_t launch_stoch_batched(const TreeView& T, const TreeCtrl& host_ctrl, c
                                  const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
                                  cudaStream_t s)
 {
-    if (nq <= 0) return cudaSuccess;
-    Params P;
-    P.T = T; P.Q = Q; P.nq = nq; P.kp = kp; P.S = S;
-    P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    P.sampling = o.sampling; P.rr = o.rr; P.coherent = o.seed_mode; P.raw_sum = o.raw_sum; P.out = out;
-    const int64_t tiles = (nq + 31) / 32;
-    int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    // stage generations 1 and 2 (the subdomains and their children), at most kStageMax nodes
-    const int32_t lo = host_ctrl.max_depth >= 1 ? host_ctrl.depth_base[1] : 0;
-    const int32_t hi = host_ctrl.depth_base[host_ctrl.max_depth >= 2 ? 3 : (host_ctrl.max_depth >= 1 ? 2 : 1)];
-    uint32_t n = (uint32_t)(hi > lo ? hi - lo : 0);
-    if (n > (uint32_t)kStageMax) n = kStageMax;
-    cudaError_t e;
-    switch (kp.kind) {
-    case SBH_COULOMB: e = launch_kind<SBH_COULOMB>(P, (unsigned)blocks, lo, n, s); break;
-    case SBH_WINDING: e = launch_kind<SBH_WINDING>(P, (unsigned)blocks, lo, n, s); break;
-    case SBH_SMOOTHDIST: e = launch_kind<SBH_SMOOTHDIST>(P, (unsigned)blocks, lo, n, s); break;
-    case SBH_AFFINE: e = launch_kind<SBH_AFFINE>(P, (unsigned)blocks, lo, n, s); break;
-    default: return cudaErrorInvalidValue;
-    }
-    if (e != cudaSuccess) return e;
-    note_launch();
-    return cudaGetLastError();
+    return launch_batched_impl<false>(T, host_ctrl, Q, nq, kp, S, seed, o, out, nullptr, 0.0f, s);
+}
+
+cudaError_t launch_stoch_batched_learned(const TreeView& T, const TreeCtrl& host_ctrl, const void* mlp_half,
+                                         float near, const float* Q, int64_t nq, const KernelParams& kp, int S,
+                                         uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s)
+{
+    return launch_batched_impl<true>(T, host_ctrl, Q, nq, kp, S, seed, o, out, mlp_half, near, s);
 }
 
 cudaError_t launch_stoch_multi(const void* set_descs, int n_sets, int64_t total_tiles, unsigned long long* counter,
@@ -515,6 +732,7 @@ cudaError_t launch_stoch_multi(const void* set_descs, int n_sets, int64_t total_
     M.counter = counter;
     Params& P = M.base;
     P.T = TreeView{}; P.Q = nullptr; P.nq = 0; P.kp = kp; P.S = S; P.out = nullptr;
+    P.mlpw = nullptr; P.near = 0.0f; P.frag = nullptr; P.learn = nullptr;
     P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     P.sampling = o.sampling; P.rr = o.rr; P.coherent = o.seed_mode; P.raw_sum = o.raw_sum;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);

@@ -1,16 +1,18 @@
 // sbh_learned.cu -- the learned child proposal: a 6-32-32-1 ReLU network that scores each child
-// of a node from query-relative geometry, trained on the residuals the estimator's own tree
-// produces, and used in place of the mass-proportional pick of Algorithm 2.
+// of a node from query-relative geometry, trained on the residuals met by the estimator's own
+// traversals, and used in place of the mass-proportional pick of Algorithm 2.
 //
-// The paper samples the path index uniformly and names importance sampling as future work
-// (Sec. 3.3); this is the project's extension. The proposal at node T is
-//   pi_c = (1 - eps) softmax(s)_c + eps m_c / m_T,   eps = 0.1,
-// so every child keeps a probability >= eps m_c / m_T > 0 and the estimator stays unbiased with
-// p(I in T) the product of the pi's along the path. Nodes with more than 64 children use the
-// mass-proportional pick. Inference reads FP16 weights and accumulates in FP32; training keeps
-// FP32 master weights (Adam) and targets pi*_c proportional to |R_c(q)|, the exact residual of
-// child c's subtree (its exact sum minus its centre-of-mass term), which is the per-level
-// proposal that minimises the variance of the child's contribution.
+// The paper samples the path index in proportion to mass and names importance sampling as future
+// work (Sec. 3.3); this is the project's extension. At a node T with 2..64 children whose centre
+// is nearer to the query than `near` cell diagonals, the proposal is
+//   pi_c = (1 - eps) softmax(clamp(s))_c + eps m_c / m_T,   eps = 0.1, scores clamped to [-40, 40];
+// elsewhere pi_c = m_c / m_T. Every child keeps a probability > 0, so the estimator stays unbiased
+// with p(I in T) the product of the pi's along the path. Training: every training query walks
+// Algorithm 2's own paths, each decision node within reach becomes a set, and its children's
+// targets are |R_c(q)|, the exact residual of the child's subtree (its exact sum minus its
+// centre-of-mass term), the per-level proposal that minimises the variance of the child's
+// contribution; cross-entropy to the normalised targets, Adam on FP32 master weights, an FP16
+// copy for inference. The estimator scores on the tensor cores (sbh_eval_batched.cu).
 //
 // Parameter layout (1313 values): W1[32][6], b1[32], W2[32][32], b2[32], w3[32], b3.
 #include <cuda_fp16.h>
@@ -24,17 +26,103 @@ namespace sbh {
 
 namespace {
 
-__global__ void k_scores(const __half* __restrict__ wg, const float* __restrict__ feats, int64_t n,
-                         float* __restrict__ out)
+// Scores of feature rows with the estimator's tensor-core scorer: one warp per chunk of 32 rows.
+constexpr int kScoreWarps = 8;
+
+__global__ void __launch_bounds__(32 * kScoreWarps) k_scores(const __half* __restrict__ wg,
+                                                            const float* __restrict__ feats, int64_t n,
+                                                            float* __restrict__ out)
 {
-    __shared__ __half w[kMlpParams];
-    for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) w[i] = wg[i];
+    __shared__ MlpFrag F;
+    __shared__ __align__(16) uint32_t A[kScoreWarps][32 * kChunkWords];
+    __shared__ float sc[kScoreWarps][32];
+    mlp_frag_fill(wg, F);
     __syncthreads();
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-        float x[6];
-        for (int k = 0; k < 6; ++k) x[k] = feats[6 * r + k];
-        out[r] = score16(w, x);
+    MlpRegs R;
+    load_mlp_regs(F, R);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t chunks = (n + 31) / 32;
+    for (int64_t c = (int64_t)blockIdx.x * kScoreWarps + warp; c < chunks; c += (int64_t)gridDim.x * kScoreWarps) {
+        const int64_t r = c * 32 + lane;
+        const bool live = r < n;
+        float x[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (live)
+            for (int k = 0; k < 6; ++k) x[k] = feats[6 * r + k];
+        store_feature_row(&A[warp][lane * kChunkWords], x, live);
+        __syncwarp();
+        const float s = score_chunk(R, A[warp], sc[warp]);
+        if (live) out[r] = s;
+        __syncwarp();
     }
+}
+
+// ------------------------------------------------------------------------------------------------
+// training sets from the estimator's own traversals: every training query walks the paths of
+// Algorithm 2 (mass-proportional picks, Eq. 5 roulette; its own random stream) and records each
+// node it takes a decision at where the network would be used. Pass 0 counts per query, pass 1
+// writes (query, node) at the query's offset. At most max_per_query sets per query.
+// ------------------------------------------------------------------------------------------------
+template <int PASS>
+__global__ void __launch_bounds__(256) k_visit(TreeView T, const float* __restrict__ Q, int nq, int samples, uint2 key,
+                                               float near, int max_per_query, int32_t* __restrict__ count,
+                                               const int64_t* __restrict__ base, int32_t* __restrict__ set_q,
+                                               int32_t* __restrict__ set_node)
+{
+    __shared__ float diam[kDiamLevels];
+    if (threadIdx.x < kDiamLevels) diam[threadIdx.x] = T.ctrl->diam[threadIdx.x];
+    __syncthreads();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nq) return;
+    const float3 q = make_float3(Q[3 * j], Q[3 * j + 1], Q[3 * j + 2]);
+    const int32_t first_sub = T.ctrl->first_sub;
+    const int n_sub = T.ctrl->n_sub;
+    int n = 0;
+    for (int ai = 0; ai < n_sub && n < max_per_query; ++ai) {
+        const int32_t a = first_sub + ai;
+        const float4 pa = __ldg(&T.pm[a]);
+        const uint32_t ma = __ldg(&T.meta[a]);
+        if (meta_kind(ma) == kPoint) continue;
+        for (int s = 0; s < samples && n < max_per_query; ++s) {
+            int32_t node = a;
+            uint32_t mT = ma;
+            float dT = dist_rn(pa.x, pa.y, pa.z, q);
+            for (uint32_t depth = 0; meta_kind(mT) != kPoint && depth < (uint32_t)kMaxDepth; ++depth) {
+                const int nc = (int)meta_nchild(mT);
+                if (learned_gate(nc, dT, near, diam[meta_level(mT)])) {
+                    if (PASS == 1) {
+                        set_q[base[j] + n] = j;
+                        set_node[base[j] + n] = node;
+                    }
+                    if (++n >= max_per_query) break;
+                }
+                const uint4 x = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)ai, (uint32_t)s, depth), key);
+                const int32_t f = __ldg(&T.fc[node]);
+                const float u = unit24(x.x);
+                int lo = 0, hi = nc - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__ldg(&T.cdf[f + mid]) <= u) lo = mid + 1;
+                    else hi = mid;
+                }
+                const int32_t c = f + lo;
+                const float4 pc = __ldg(&T.pm[c]);
+                const uint32_t mc = __ldg(&T.meta[c]);
+                const float dc = dist_rn(pc.x, pc.y, pc.z, q);
+                const float p = rr_prob_rn(dT, diam[meta_level(mT)], dc, diam[meta_level(mc)]);
+                if (unit24(x.y) >= p) break;
+                node = c;
+                mT = mc;
+                dT = dc;
+            }
+        }
+    }
+    if (PASS == 0) count[j] = n;
+}
+
+__global__ void k_set_rows(TreeView T, const int32_t* __restrict__ set_node, int64_t n_sets, int64_t* __restrict__ rows)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n_sets) rows[i] = (int64_t)meta_nchild(__ldg(&T.meta[set_node[i]]));
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -76,22 +164,21 @@ __device__ __forceinline__ double node_value64(const TreeView& T, int32_t v, flo
     }
 }
 
-// one warp per (query, subdomain set); set s covers rows set_off[s] .. set_off[s+1]-1
+// one warp per decision set s = (query set_q[s], node set_node[s]); rows set_off[s] ..
 template <int KIND>
 __global__ void k_dataset(TreeView T, const float4* __restrict__ spw, const float4* __restrict__ snrm,
-                          const float* __restrict__ Q, int nq, const int32_t* __restrict__ set_node, int n_node_sets,
-                          const int64_t* __restrict__ set_off, KernelParams kp, float* __restrict__ feats,
-                          float* __restrict__ targets)
+                          const float* __restrict__ Q, const int32_t* __restrict__ set_q,
+                          const int32_t* __restrict__ set_node, int64_t n_sets, const int64_t* __restrict__ set_off,
+                          KernelParams kp, float* __restrict__ feats, float* __restrict__ targets)
 {
     __shared__ float diam[kDiamLevels];
     if (threadIdx.x < kDiamLevels) diam[threadIdx.x] = T.ctrl->diam[threadIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int64_t n_sets = (int64_t)nq * n_node_sets;
     for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < n_sets;
          s += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-        const int64_t j = s / n_node_sets;
-        const int32_t a = set_node[s % n_node_sets];
+        const int64_t j = set_q[s];
+        const int32_t a = set_node[s];
         const float3 q = make_float3(Q[3 * j], Q[3 * j + 1], Q[3 * j + 2]);
         const uint32_t ma = __ldg(&T.meta[a]);
         const float4 pa = __ldg(&T.pm[a]);
@@ -260,9 +347,9 @@ cudaError_t mlp_sync_half(MlpState& M, cudaStream_t s)
 cudaError_t mlp_scores(const MlpState& M, const float* feats, int64_t n, float* out, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
-    int64_t blocks = (n + 255) / 256;
+    int64_t blocks = ((n + 31) / 32 + kScoreWarps - 1) / kScoreWarps;
     if (blocks > 152 * 8) blocks = 152 * 8;
-    k_scores<<<(unsigned)blocks, 256, 0, s>>>(M.wh, feats, n, out);
+    k_scores<<<(unsigned)blocks, 32 * kScoreWarps, 0, s>>>(M.wh, feats, n, out);
     note_launch();
     return cudaGetLastError();
 }
@@ -291,19 +378,41 @@ cudaError_t mlp_adam_step(MlpState& M, float lr, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t mlp_dataset(const sbh_tree* tree, const float* Q, int nq, const int32_t* set_node, int n_node_sets,
-                        const int64_t* set_off, const KernelParams& kp, float* feats, float* targets, cudaStream_t s)
+cudaError_t mlp_visit(const TreeView& T, const float* Q, int nq, int samples, uint64_t seed, float near,
+                      int max_per_query, int32_t* count, const int64_t* base, int32_t* set_q, int32_t* set_node,
+                      cudaStream_t s)
 {
+    if (nq <= 0) return cudaSuccess;
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const unsigned b = (unsigned)((nq + 255) / 256);
+    if (base == nullptr) k_visit<0><<<b, 256, 0, s>>>(T, Q, nq, samples, key, near, max_per_query, count, nullptr, nullptr, nullptr);
+    else k_visit<1><<<b, 256, 0, s>>>(T, Q, nq, samples, key, near, max_per_query, nullptr, base, set_q, set_node);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_set_rows(const TreeView& T, const int32_t* set_node, int64_t n_sets, int64_t* rows, cudaStream_t s)
+{
+    if (n_sets <= 0) return cudaSuccess;
+    k_set_rows<<<(unsigned)((n_sets + 255) / 256), 256, 0, s>>>(T, set_node, n_sets, rows);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_dataset(const sbh_tree* tree, const float* Q, const int32_t* set_q, const int32_t* set_node,
+                        int64_t n_sets, const int64_t* set_off, const KernelParams& kp, float* feats, float* targets,
+                        cudaStream_t s)
+{
+    if (n_sets <= 0) return cudaSuccess;
     const TreeView T = tree->t4.view();
-    const int64_t warps = (int64_t)nq * n_node_sets;
-    int64_t blocks = (warps * 32 + 255) / 256;
+    int64_t blocks = (n_sets * 32 + 255) / 256;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    const unsigned b = (unsigned)(blocks < 1 ? 1 : blocks);
+    const unsigned b = (unsigned)blocks;
     switch (kp.kind) {
-    case SBH_COULOMB: k_dataset<SBH_COULOMB><<<b, 256, 0, s>>>(T, tree->spw, tree->snrm, Q, nq, set_node, n_node_sets, set_off, kp, feats, targets); break;
-    case SBH_WINDING: k_dataset<SBH_WINDING><<<b, 256, 0, s>>>(T, tree->spw, tree->snrm, Q, nq, set_node, n_node_sets, set_off, kp, feats, targets); break;
-    case SBH_SMOOTHDIST: k_dataset<SBH_SMOOTHDIST><<<b, 256, 0, s>>>(T, tree->spw, tree->snrm, Q, nq, set_node, n_node_sets, set_off, kp, feats, targets); break;
-    case SBH_AFFINE: k_dataset<SBH_AFFINE><<<b, 256, 0, s>>>(T, tree->spw, tree->snrm, Q, nq, set_node, n_node_sets, set_off, kp, feats, targets); break;
+    case SBH_COULOMB: k_dataset<SBH_COULOMB><<<b, 256, 0, s>>>(T, tree->spw, tree->snrm, Q, set_q, set_node, n_sets, set_off, kp, feats, targets); break;
+    case SBH_WINDING: k_dataset<SBH_WINDING><<<b, 256, 0, s>>>(T, tree->spw, tree->snrm, Q, set_q, set_node, n_sets, set_off, kp, feats, targets); break;
+    case SBH_SMOOTHDIST: k_dataset<SBH_SMOOTHDIST><<<b, 256, 0, s>>>(T, tree->spw, tree->snrm, Q, set_q, set_node, n_sets, set_off, kp, feats, targets); break;
+    case SBH_AFFINE: k_dataset<SBH_AFFINE><<<b, 256, 0, s>>>(T, tree->spw, tree->snrm, Q, set_q, set_node, n_sets, set_off, kp, feats, targets); break;
     default: return cudaErrorInvalidValue;
     }
     note_launch();
