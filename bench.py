@@ -459,6 +459,15 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
         return best
 
     best = bh_time_at(err_s)
+    learned = learned_proposal(sbh, wl, tree, Q, idx, ref, seed, kk, timed) if LEARNED_NEAR > 0 else None
+    if learned is not None:
+        variants["learned_proposal"] = learned
+        # the mass-proportional estimator's time at the learned proposal's error, from its S = 1, 2, 4 rows
+        mass_pts = [(err_s, eval_ms)] + [(v["median_rel_err"], v["ms"]) for v in extra.values()]
+        t_mass, extrap_m = interp_loglog(learned["median_rel_err"], [p[0] for p in mass_pts], [p[1] for p in mass_pts])
+        learned["mass_ms_at_equal_error"] = t_mass
+        learned["mass_extrapolated"] = extrap_m
+        learned["speedup_vs_mass"] = t_mass / learned["ms"]
     for v in list(extra.values()) + list(variants.values()):
         t_bh, extrap, _ = bh_time_at(v["median_rel_err"])
         v["bh_ms_at_equal_error"] = t_bh
@@ -469,6 +478,30 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
             "speedup_vs_bh_at_equal_median_error": best[0] / eval_ms,
             "error_reference": "GPU brute force with FP64 tile accumulation on 65536 random queries",
             "time_basis": "evaluation kernels only, trees prebuilt (the paper excludes building)"}
+
+
+LEARNED_NEAR = 0.5  # gate of the learned proposal in cell diagonals (0 = skip the learned row)
+
+
+def learned_proposal(sbh, wl, tree, Q, idx, ref, seed, kk, timed):
+    """Train the learned child proposal on 1024 random queries in the sources' bounding box (the
+    residuals the estimator's own paths meet there), then time it at S = 1 on the full query set."""
+    import torch
+    lo, hi = wl.points.min(0), wl.points.max(0)
+    qt = np.random.default_rng(5).uniform(lo - 0.05 * (hi - lo), hi + 0.05 * (hi - lo), (1024, 3)).astype(np.float32)
+    net = sbh.sbh_mlp_create(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = sbh.sbh_mlp_train(net, tree, torch.from_numpy(qt).to(Q.device), near=LEARNED_NEAR, steps=300, lr=3e-3,
+                               **kk)
+    train_s = time.perf_counter() - t0
+    out = sbh.sbh_eval_learned(tree, net, Q, seed=seed, near=LEARNED_NEAR, **kk)
+    ms = timed(lambda: sbh.sbh_eval_learned(tree, net, Q, seed=seed, near=LEARNED_NEAR, out=out, **kk), 2)
+    err = float(np.median(rel_error(wl.kernel, out[idx].cpu().numpy(), ref)))
+    return {"ms": ms, "median_rel_err": err, "near": LEARNED_NEAR, "train_s": train_s,
+            "train": {"queries": 1024, "adam_steps": 300, "lr": 3e-3, "loss_first": float(losses[0]),
+                      "loss_last": float(losses[-1])},
+            "scorer": "tensor cores (mma.sync m16n8k16, FP16 operands, FP32 accumulation)"}
 
 
 # ------------------------------------------------------------------------------------------------

@@ -21,6 +21,14 @@ namespace sbh {
 
 namespace {
 
+// resident blocks per SM the register budget is set for, and the most nodes staged per block
+#ifndef SBH_BATCHED_MIN_BLOCKS
+#define SBH_BATCHED_MIN_BLOCKS 3
+#endif
+#ifndef SBH_STAGE_MAX
+#define SBH_STAGE_MAX 2048
+#endif
+
 constexpr int kWarpsPerBlock = 8;
 constexpr int kRing = 64;  // ring capacity per warp; at most 63 tasks wait at any time
 constexpr uint32_t kRingMask = kRing - 1;
@@ -51,7 +59,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << lane_id()) - 1
 
 // The subdomains and their children (node generations 1 and 2) are read by every query: each
 // block copies them (up to kStageMax nodes) into shared memory at start and reads them there.
-constexpr int kStageMax = 2048;
+constexpr int kStageMax = SBH_STAGE_MAX;
 
 struct Stage {
     int32_t lo;       // first staged node id
@@ -559,7 +567,7 @@ constexpr size_t learned_smem_bytes()
 }
 
 template <int KIND, bool LEARNED>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, LEARNED ? 2 : 3)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, LEARNED ? 2 : SBH_BATCHED_MIN_BLOCKS)
     k_stoch_batched(Params P, int32_t stage_lo, uint32_t stage_n)
 {
     __shared__ WarpState s_state[kWarpsPerBlock];
