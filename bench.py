@@ -423,7 +423,7 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
         return float(np.median(ts))
 
     extra = {}
-    for s2 in (2, 4):
+    for s2 in (2, 3, 4):
         o2 = sbh.sbh_eval(tree, Q, samples_per_subdomain=s2, seed=seed, **kk)
         extra[f"S{s2}"] = {"ms": timed(lambda: sbh.sbh_eval(tree, Q, samples_per_subdomain=s2, seed=seed, out=o2, **kk), 2),
                            "median_rel_err": float(np.median(rel_error(wl.kernel, o2[idx].cpu().numpy(), ref)))}
@@ -607,7 +607,7 @@ def run_batched(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="winding",

@@ -235,6 +235,21 @@ SBH_API sbh_status sbh_eval_learned(const sbh_tree* tree, const sbh_mlp* net, co
                                     const sbh_eval_opts* opts, float near, float* out, void* stream);
 SBH_API void sbh_mlp_free(sbh_mlp* net);
 
+/* Device memory. Every buffer the library holds (trees, scratch, plans, networks) comes from a
+ * stream-ordered pool of its own, or, once set, from the caller's allocator: alloc(bytes, stream,
+ * ctx) returns a device pointer aligned to 256 bytes that is usable in stream order on `stream`
+ * (NULL: out of memory, reported as SBH_ENOMEM); free(ptr, stream, ctx) gives it back in stream
+ * order. Both functions or neither (NULL, NULL: back to the pool); a block is always returned to
+ * the allocator that gave it. Set the allocator while no library call is in flight. */
+typedef void* (*sbh_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*sbh_free_fn)(void* ptr, void* stream, void* ctx);
+SBH_API sbh_status sbh_set_allocator(sbh_alloc_fn alloc, sbh_free_fn free_fn, void* ctx);
+/* Cap on the bytes the library holds at once (0: none). An allocation that would pass it fails
+ * and the call returns SBH_ENOMEM with nothing leaked. */
+SBH_API sbh_status sbh_set_memory_limit(uint64_t bytes);
+/* Bytes the library holds now. */
+SBH_API uint64_t sbh_memory_in_use(void);
+
 /* Deterministic Barnes-Hut (Algorithm 1) on the 8-ary tree: a node is used whole when it is a
  * single point or ||q - p_a|| / |B_a| >= beta = 1 / theta (theta = 0 gives the exact sum).
  * warp_vote = 1 takes the decision jointly for the 32 queries of a warp (a node is opened when

@@ -114,6 +114,11 @@ def load_library():
         lib.sbh_mlp_train.argtypes = [P, P, P, i64, _Kernel, C.c_float, i32, C.c_float, P, P]
         lib.sbh_eval_learned.argtypes = [P, P, P, i64, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts), C.c_float, P,
                                          P]
+        lib.sbh_set_allocator.argtypes = [P, P, P]
+        lib.sbh_set_allocator.restype = i32
+        lib.sbh_set_memory_limit.argtypes = [C.c_uint64]
+        lib.sbh_set_memory_limit.restype = i32
+        lib.sbh_memory_in_use.restype = C.c_uint64
         lib.sbh_mlp_free.argtypes = [P]
         lib.sbh_mlp_free.restype = None
         for f in ("sbh_build", "sbh_eval", "sbh_eval_count", "sbh_eval_grad", "sbh_eval_bh", "sbh_eval_brute",
@@ -571,3 +576,57 @@ def sbh_eval_learned(tree: Tree, net: Mlp, queries, kernel="coulomb", samples_pe
                                            C.byref(opts) if opts is not None else None, C.c_float(near),
                                            _dev(out, "out"), _stream(stream)))
     return out
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+_allocator_keepalive = None
+
+
+def sbh_set_allocator(alloc=None, free=None) -> None:
+    """Route the library's device memory through alloc(bytes, stream_handle) -> int pointer and
+    free(ptr, stream_handle); None, None restores the library's own pool."""
+    global _allocator_keepalive
+    lib = load_library()
+    if (alloc is None) != (free is None):
+        raise ValueError("give both allocator functions or neither")
+    if alloc is None:
+        _check(lib.sbh_set_allocator(None, None, None))
+        _allocator_keepalive = None
+        return
+
+    def _a(nbytes, stream, ctx):
+        try:
+            return int(alloc(int(nbytes), stream or 0)) or None
+        except Exception:
+            return None
+
+    def _f(ptr, stream, ctx):
+        free(int(ptr), stream or 0)
+
+    cbs = (ALLOC_FN(_a), FREE_FN(_f))
+    _check(lib.sbh_set_allocator(C.cast(cbs[0], C.c_void_p), C.cast(cbs[1], C.c_void_p), None))
+    _allocator_keepalive = cbs
+
+
+def use_torch_allocator() -> None:
+    """Take the library's device memory from PyTorch's caching allocator (stream-ordered on the
+    stream of each library call)."""
+    import torch
+
+    def alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, torch.cuda.current_device(), stream)
+
+    def free(ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    sbh_set_allocator(alloc, free)
+
+
+def sbh_set_memory_limit(nbytes: int) -> None:
+    """Cap the device bytes the library holds at once (0: no cap); beyond it calls fail with SBH_ENOMEM."""
+    _check(load_library().sbh_set_memory_limit(C.c_uint64(int(nbytes))))
+
+
+def sbh_memory_in_use() -> int:
+    return int(load_library().sbh_memory_in_use())

@@ -586,6 +586,23 @@ void sbh_mlp_free(sbh_mlp* net)
     delete net;
 }
 
+sbh_status sbh_set_allocator(sbh_alloc_fn alloc, sbh_free_fn free_fn, void* ctx)
+{
+    g_err[0] = 0;
+    if ((alloc == nullptr) != (free_fn == nullptr)) return fail(SBH_EINVAL, "set both allocator functions or neither");
+    sbh::set_allocator(alloc, free_fn, ctx);
+    return SBH_OK;
+}
+
+sbh_status sbh_set_memory_limit(uint64_t bytes)
+{
+    g_err[0] = 0;
+    sbh::set_memory_limit(bytes);
+    return SBH_OK;
+}
+
+uint64_t sbh_memory_in_use(void) { return sbh::memory_in_use(); }
+
 unsigned long long sbh_kernel_launches(void) { return sbh::g_launches.load(std::memory_order_relaxed); }
 
 sbh_status sbh_eval_bh(sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel, float theta,
@@ -605,7 +622,13 @@ sbh_status sbh_eval_bh(sbh_tree* tree, const float* queries, int64_t nq, sbh_ker
         // the root cube of t2.ctrl was written by sbh_build; alloc_tree keeps that block
         cudaError_t e = sbh::alloc_tree(tree->t2, tree->n, tree->has_normals != 0, true, s);
         if (e == cudaSuccess) e = sbh::build_tree(tree, tree->t2, tree->lcp2, sbh::kMaxLevel2, 1, true, s);
-        if (e != cudaSuccess) return cuda_fail(e, "sbh_eval_bh tree build");
+        if (e != cudaSuccess) {  // give back what was taken, keep the control block with the root cube
+            sbh::TreeCtrl* ctrl = tree->t2.ctrl;
+            tree->t2.ctrl = nullptr;
+            sbh::free_tree(tree->t2, s);
+            tree->t2.ctrl = ctrl;
+            return cuda_fail(e, "sbh_eval_bh tree build");
+        }
         tree->stream = s;
     }
     if (nq == 0) return SBH_OK;

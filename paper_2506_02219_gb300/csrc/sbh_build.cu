@@ -16,6 +16,9 @@
 // Node ids are generation-major (breadth-first): every node's children are contiguous, in
 // Morton order, and the top generations that every query reads sit at the front of each array.
 #include <cuda_runtime.h>
+
+#include <mutex>
+#include <unordered_map>
 #include <stdint.h>
 
 #include "sbh_build.cuh"
@@ -34,15 +37,44 @@ inline unsigned grid_for(int64_t n, int per_block = kThreads, unsigned cap = 152
 }  // namespace
 
 // ----------------------------------------------------------------------------------------------
-// memory pool
+// device memory: the library's stream-ordered pool, or the caller's allocator; an optional cap on
+// the bytes the library holds at once (allocations beyond it fail as out of memory)
 // ----------------------------------------------------------------------------------------------
-static cudaMemPool_t g_pool[64];
-static bool g_pool_ready[64];
+namespace {
+struct Block {
+    size_t bytes;
+    sbh_free_fn free_fn;  // nullptr: the library's pool
+    void* ctx;
+};
+std::mutex g_mem_mutex;
+cudaMemPool_t g_pool[64];
+bool g_pool_ready[64];
+sbh_alloc_fn g_alloc_fn = nullptr;
+sbh_free_fn g_free_fn = nullptr;
+void* g_alloc_ctx = nullptr;
+uint64_t g_limit = 0;
+uint64_t g_in_use = 0;
+std::unordered_map<void*, Block> g_blocks;
+}  // namespace
 
 cudaError_t dalloc(void** p, size_t bytes, cudaStream_t s)
 {
     *p = nullptr;
     if (bytes == 0) bytes = 16;
+    std::lock_guard<std::mutex> lock(g_mem_mutex);
+    if (g_limit && g_in_use + bytes > g_limit) return cudaErrorMemoryAllocation;
+    if (g_alloc_fn) {
+        void* q = g_alloc_fn(bytes, (void*)s, g_alloc_ctx);
+        if (!q) return cudaErrorMemoryAllocation;
+        if (((uintptr_t)q & 255u) != 0) {  // misaligned: hand it back and fail
+            g_free_fn(q, (void*)s, g_alloc_ctx);
+            return cudaErrorMisalignedAddress;
+        }
+        *p = q;
+        g_blocks[q] = Block{bytes, g_free_fn, g_alloc_ctx};
+        g_in_use += bytes;
+        return cudaSuccess;
+    }
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -58,12 +90,48 @@ cudaError_t dalloc(void** p, size_t bytes, cudaStream_t s)
         cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
         g_pool_ready[dev] = true;
     }
-    return cudaMallocFromPoolAsync(p, bytes, g_pool[dev], s);
+    e = cudaMallocFromPoolAsync(p, bytes, g_pool[dev], s);
+    if (e != cudaSuccess) return e;
+    g_blocks[*p] = Block{bytes, nullptr, nullptr};
+    g_in_use += bytes;
+    return cudaSuccess;
 }
 
 void dfree(void* p, cudaStream_t s)
 {
-    if (p) cudaFreeAsync(p, s);
+    if (!p) return;
+    Block b{0, nullptr, nullptr};
+    {
+        std::lock_guard<std::mutex> lock(g_mem_mutex);
+        auto it = g_blocks.find(p);
+        if (it != g_blocks.end()) {
+            b = it->second;
+            g_in_use -= b.bytes;
+            g_blocks.erase(it);
+        }
+    }
+    if (b.free_fn) b.free_fn(p, (void*)s, b.ctx);
+    else cudaFreeAsync(p, s);
+}
+
+void set_allocator(sbh_alloc_fn a, sbh_free_fn f, void* ctx)
+{
+    std::lock_guard<std::mutex> lock(g_mem_mutex);
+    g_alloc_fn = a;
+    g_free_fn = f;
+    g_alloc_ctx = ctx;
+}
+
+void set_memory_limit(uint64_t bytes)
+{
+    std::lock_guard<std::mutex> lock(g_mem_mutex);
+    g_limit = bytes;
+}
+
+uint64_t memory_in_use()
+{
+    std::lock_guard<std::mutex> lock(g_mem_mutex);
+    return g_in_use;
 }
 
 // ----------------------------------------------------------------------------------------------
@@ -662,6 +730,34 @@ __global__ void k_skip(const int32_t* __restrict__ parent, const int32_t* __rest
         if (e_ != cudaSuccess) return e_;        \
     } while (0)
 
+// Scratch buffers of one build step: whatever is still held when the step returns (on success or
+// on an error part way) goes back in stream order; keep() hands a buffer over to the tree.
+struct ScratchSet {
+    cudaStream_t s;
+    void* p[8] = {};
+    int n = 0;
+    explicit ScratchSet(cudaStream_t st) : s(st) {}
+    ScratchSet(const ScratchSet&) = delete;
+    ScratchSet& operator=(const ScratchSet&) = delete;
+    template <class T>
+    cudaError_t alloc(T** q, size_t bytes)
+    {
+        if (n == 8) return cudaErrorInvalidValue;
+        const cudaError_t e = dalloc((void**)q, bytes, s);
+        if (e == cudaSuccess) p[n++] = (void*)*q;
+        return e;
+    }
+    void keep(const void* q)
+    {
+        for (int i = 0; i < n; ++i)
+            if (p[i] == q) p[i] = nullptr;
+    }
+    ~ScratchSet()
+    {
+        for (int i = 0; i < n; ++i) dfree(p[i], s);
+    }
+};
+
 cudaError_t alloc_tree(DeviceTree& D, int64_t n, bool with_dip, bool with_skip, cudaStream_t s)
 {
     const int64_t cap = 2 * n + 1;
@@ -692,8 +788,9 @@ cudaError_t build_sorted(sbh_tree* T, const float* pts, const float* w, const fl
                          int* bad_points, int* bad_weights)
 {
     const int64_t n = T->n;
+    ScratchSet guard(s);
     int* scratch = nullptr;
-    SBH_TRY(dalloc((void**)&scratch, 8 * sizeof(int), s));
+    SBH_TRY(guard.alloc(&scratch, 8 * sizeof(int)));
     k_bounds_init<<<1, 32, 0, s>>>(scratch);
     note_launch();
     k_bounds<<<grid_for(n), kThreads, 0, s>>>(pts, w, n, scratch);
@@ -703,26 +800,22 @@ cudaError_t build_sorted(sbh_tree* T, const float* pts, const float* w, const fl
     SBH_TRY(cudaStreamSynchronize(s));
     *bad_points = host[6];
     *bad_weights = host[7];
-    if (host[6] || host[7]) {
-        dfree(scratch, s);
-        return cudaSuccess;
-    }
+    if (host[6] || host[7]) return cudaSuccess;
     k_root_cube<<<1, 32, 0, s>>>(scratch, T->t4.ctrl, T->t2.ctrl);
     note_launch();
     SBH_TRY(cudaGetLastError());
-    dfree(scratch, s);
 
     uint64_t *k0 = nullptr, *k1 = nullptr;
     int32_t *v0 = nullptr, *v1 = nullptr;
     const int ntiles = (int)((n + kSortTile - 1) / kSortTile);
     const int64_t nhist = (int64_t)256 * ntiles;
     int *hist = nullptr, *tmp = nullptr;
-    SBH_TRY(dalloc((void**)&k0, n * sizeof(uint64_t), s));
-    SBH_TRY(dalloc((void**)&k1, n * sizeof(uint64_t), s));
-    SBH_TRY(dalloc((void**)&v0, n * sizeof(int32_t), s));
-    SBH_TRY(dalloc((void**)&v1, n * sizeof(int32_t), s));
-    SBH_TRY(dalloc((void**)&hist, nhist * sizeof(int), s));
-    SBH_TRY(dalloc((void**)&tmp, scan_temp_ints(nhist) * sizeof(int), s));
+    SBH_TRY(guard.alloc(&k0, n * sizeof(uint64_t)));
+    SBH_TRY(guard.alloc(&k1, n * sizeof(uint64_t)));
+    SBH_TRY(guard.alloc(&v0, n * sizeof(int32_t)));
+    SBH_TRY(guard.alloc(&v1, n * sizeof(int32_t)));
+    SBH_TRY(guard.alloc(&hist, nhist * sizeof(int)));
+    SBH_TRY(guard.alloc(&tmp, scan_temp_ints(nhist) * sizeof(int)));
     k_morton<<<grid_for(n), kThreads, 0, s>>>(pts, n, T->t4.ctrl, k0, v0);
     note_launch();
     for (int pass = 0; pass < 8; ++pass) {
@@ -738,10 +831,8 @@ cudaError_t build_sorted(sbh_tree* T, const float* pts, const float* w, const fl
     SBH_TRY(cudaGetLastError());
     T->code = k0;
     T->perm = v0;
-    dfree(k1, s);
-    dfree(v1, s);
-    dfree(hist, s);
-    dfree(tmp, s);
+    guard.keep(k0);
+    guard.keep(v0);
 
     SBH_TRY(dalloc((void**)&T->spw, n * sizeof(float4), s));
     if (nrm) SBH_TRY(dalloc((void**)&T->snrm, n * sizeof(float4), s));
@@ -760,12 +851,13 @@ cudaError_t build_tree(sbh_tree* T, DeviceTree& D, const uint8_t* lcp, int max_l
     const int64_t n = T->n;
     D.max_level = max_level;
     D.level_shift = level_shift;
+    ScratchSet guard(s);
     int32_t *cid = nullptr, *flag = nullptr, *scan = nullptr, *tmp = nullptr, *rmin = nullptr;
-    SBH_TRY(dalloc((void**)&cid, n * sizeof(int32_t), s));
-    SBH_TRY(dalloc((void**)&flag, n * sizeof(int32_t), s));
-    SBH_TRY(dalloc((void**)&scan, n * sizeof(int32_t), s));
-    SBH_TRY(dalloc((void**)&tmp, scan_temp_ints(n) * sizeof(int32_t), s));
-    SBH_TRY(dalloc((void**)&rmin, sizeof(int32_t), s));
+    SBH_TRY(guard.alloc(&cid, n * sizeof(int32_t)));
+    SBH_TRY(guard.alloc(&flag, n * sizeof(int32_t)));
+    SBH_TRY(guard.alloc(&scan, n * sizeof(int32_t)));
+    SBH_TRY(guard.alloc(&tmp, scan_temp_ints(n) * sizeof(int32_t)));
+    SBH_TRY(guard.alloc(&rmin, sizeof(int32_t)));
 
     BuildArrays B;
     B.nb = D.nb; B.ne = D.ne; B.fc = D.fc; B.parent = D.parent; B.meta = D.meta; B.minl = D.minl;
@@ -809,7 +901,6 @@ cudaError_t build_tree(sbh_tree* T, DeviceTree& D, const uint8_t* lcp, int max_l
         }
     }
     SBH_TRY(cudaGetLastError());
-    dfree(cid, s); dfree(flag, s); dfree(scan, s); dfree(tmp, s); dfree(rmin, s);
     D.built = true;
     return cudaSuccess;
 }

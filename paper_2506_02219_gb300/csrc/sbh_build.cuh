@@ -36,9 +36,12 @@ struct DeviceTree {
     }
 };
 
-// stream-ordered device allocation from the library's memory pool
+// stream-ordered device allocation: the library's memory pool or the caller's allocator
 cudaError_t dalloc(void** p, size_t bytes, cudaStream_t s);
 void dfree(void* p, cudaStream_t s);
+void set_allocator(sbh_alloc_fn a, sbh_free_fn f, void* ctx);
+void set_memory_limit(uint64_t bytes);
+uint64_t memory_in_use();
 
 int64_t scan_temp_ints(int64_t n);
 void scan_exclusive(const int* in, int* out, int64_t n, int* temp, cudaStream_t s);

@@ -153,13 +153,16 @@ class _Box:
         return uv * self.h + self.c, nrm
 
 
-def shape_union(n: int, seed: int, n_ellipsoids: int = 8, n_boxes: int = 0, rescale: bool = True):
+def shape_union(n: int, seed: int, n_ellipsoids: int = 8, n_boxes: int = 0, rescale: bool = True,
+                heavy_fraction: float = 0.0, heavy_factor: float = 5.0):
     """n area-uniform samples on the surface of a union of random ellipsoids (centres
     U[-0.6, 0.6]^3, semi-axes U[0.15, 0.5], random rotations) and axis-aligned boxes (centres
     U[-0.6, 0.6]^3, half-extents U[0.1, 0.4]). Candidates are drawn on each shape in proportion
     to its area, those inside another shape are dropped, until n remain. Each sample carries the
     area weight A_i / N_i (shape area over candidates drawn on that shape) and its outward normal.
-    With rescale, the set is scaled isotropically to fit [-1, 1]^3."""
+    With rescale, the set is scaled isotropically to fit [-1, 1]^3. heavy_fraction > 0 multiplies
+    the weights of that fraction of the samples (a seeded random subset) by heavy_factor: a few
+    heavier sources among uniform ones, as the paper's teaser scene has."""
     rng = np.random.default_rng(seed)
     shapes = []
     for _ in range(n_ellipsoids):
@@ -198,6 +201,10 @@ def shape_union(n: int, seed: int, n_ellipsoids: int = 8, n_boxes: int = 0, resc
         s = 2.0 / float(np.max(hi - lo)) * 0.999
         P = (P - ctr) * s
         w = w * s * s
+    if heavy_fraction > 0.0:
+        heavy = np.random.default_rng(seed + 7).permutation(n)[: int(round(heavy_fraction * n))]
+        w = w.copy()
+        w[heavy] *= heavy_factor
     return P.astype(np.float32), w.astype(np.float32), Nv.astype(np.float32)
 
 
