@@ -529,16 +529,22 @@ static float ffratio32(const otree *t, int64_t v, const float q[3])
     return dist32(&t->com32[3 * v], q) / diam32(t, t->level[v]);
 }
 
-/* Russian-roulette continue probability into child c of node v, Eq. 5, in FP32 */
-static float rr_prob32(const otree *t, int64_t v, int64_t c, const float q[3], int rr)
+/* Eq. 5 for the step from node v into its child c with the draw u: the path continues iff u < p,
+ * p = min(1, max(1, beta~_v) / beta~_c), beta~ = ||q - p~|| / |B|. The child's cell is exactly
+ * 2^(-(bits/3)(l_c - l_v)) times the node's, so p = min(1, X / d_c) with
+ * X = max(d_v, |B_v|) 2^(-(bits/3)(l_c - l_v)) (exact in FP32), and u < p is u d_c < X, compared
+ * exactly (the product of a 24-bit u and an FP32 d_c is exact in FP64). On a continue *p gets
+ * fl32(X / d_c) capped at 1, the factor of p_rr. */
+static int rr_continue32(const otree *t, int64_t v, int64_t c, const float q[3], int rr, float u, float *p)
 {
-    if (rr == RR_OFF) return 1.0f;
-    if (rr == RR_HALF) return 0.5f;
-    float bt = ffratio32(t, v, q);
-    float bc = ffratio32(t, c, q);
-    float num = bt > 1.0f ? bt : 1.0f;
-    float r = num / bc;  /* bc == 0 gives +inf, hence probability 1 */
-    return r < 1.0f ? r : 1.0f;
+    if (rr == RR_OFF) { *p = 1.0f; return 1; }
+    if (rr == RR_HALF) { *p = 0.5f; return u < 0.5f; }
+    float dv = dist32(&t->com32[3 * v], q), dc = dist32(&t->com32[3 * c], q);
+    float bv = diam32(t, t->level[v]);
+    float X = ldexpf(dv > bv ? dv : bv, -(t->bits / 3) * (t->level[c] - t->level[v]));
+    if (!((double)u * (double)dc < (double)X)) return 0;
+    *p = dc > X ? X / dc : 1.0f;
+    return 1;
 }
 
 /* Eq. 5 in exact arithmetic (FP64), used by the enumeration */
@@ -657,8 +663,8 @@ SBHO_API void sbho_bh(const void *h, const sbho_kernel *k, const float *queries,
 /*     for s in 1..S: T = a, k = 0, p_rr = 1                                                   */
 /*       while T is not a leaf:                                                                */
 /*         c   = child of T containing I            (drawn lazily, word 0)                     */
-/*         p   = Eq. 5 for (T, c)                   (FP32)                                     */
-/*         if rand >= p: stop                       (word 1)                                   */
+/*         p   = Eq. 5 for (T, c); stop unless      (exact test rand < p on FP32 inputs,       */
+/*               rand < p                            word 1)                                    */
 /*         Delta = Eq. 6 at T;  p_agg = p(I in T);  p_rr *= p                                  */
 /*         F_a += Delta / (p_agg p_rr);  T = c;  k += 1                                        */
 /*     F += CV_a + F_a / S                                                                     */
@@ -698,8 +704,8 @@ SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *quer
                     uint32_t x[4];
                     sbho_philox4x32_10(ctr, key, x);
                     int64_t c = pick_child(t, T, x[0], sampling);
-                    float p = rr_prob32(t, T, c, q32, rr);
-                    if (unit24f(x[1]) >= p) break;
+                    float p;
+                    if (!rr_continue32(t, T, c, q32, rr, unit24f(x[1]), &p)) break;
                     double delta = swap_delta(t, k, T, q);
                     double pagg = p_in(t, T, a, sampling);
                     prr *= (double)p;
@@ -754,8 +760,8 @@ SBHO_API void sbho_replay_grad(const void *h, const sbho_kernel *k, const float 
                     uint32_t x[4];
                     sbho_philox4x32_10(ctr, key, x);
                     int64_t ch = pick_child(t, T, x[0], sampling);
-                    float p = rr_prob32(t, T, ch, q32, rr);
-                    if (unit24f(x[1]) >= p) break;
+                    float p;
+                    if (!rr_continue32(t, T, ch, q32, rr, unit24f(x[1]), &p)) break;
                     double pagg = p_in(t, T, a, sampling);
                     prr *= (double)p;
                     double wgt = 1.0 / (pagg * prr * (double)S);

@@ -167,10 +167,9 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                     const float4 pc = __ldg(&T.pm[c]);
                     const uint32_t mc = __ldg(&T.meta[c]);
                     const float dc = dist_rn(pc.x, pc.y, pc.z, q);
-                    float p;
-                    if (rr == 0) p = rr_prob_rn(dT, sdiam[meta_level(mT)], dc, sdiam[meta_level(mc)]);
-                    else p = (rr == 1) ? 1.0f : 0.5f;
-                    if (unit24(x.y) >= p) break;
+                    float p = 1.0f;
+                    if (!rr_continue(rr, unit24(x.y), dT, sdiam[meta_level(mT)], meta_level(mT), dc, meta_level(mc), p))
+                        break;
                     prr *= p;
                     const float pagg = LEARNED ? ppath : wT / wa;
                     const float w = 1.0f / (pagg * prr) * invS;

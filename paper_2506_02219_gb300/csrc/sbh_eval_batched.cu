@@ -28,6 +28,10 @@ namespace {
 #ifndef SBH_STAGE_MAX
 #define SBH_STAGE_MAX 2048
 #endif
+// child records in flight per lane in a swap task (2 or 4)
+#ifndef SBH_SWAP_WAYS
+#define SBH_SWAP_WAYS 2
+#endif
 
 constexpr int kWarpsPerBlock = 8;
 constexpr int kRing = 64;  // ring capacity per warp; at most 63 tasks wait at any time
@@ -346,10 +350,9 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
         const float4 pc = ld_pm(T, S, child);
         const uint32_t mc = ld_meta(T, S, child);
         dc = dist_rn(pc.x, pc.y, pc.z, q);
-        float p;
-        if (P.rr == 0) p = rr_prob_rn(dT, sdiam[meta_level(mT)], dc, sdiam[meta_level(mc)]);
-        else p = (P.rr == 1) ? 1.0f : 0.5f;
-        cont = unit24(x.y) < p;
+        float p = 1.0f;
+        const uint32_t lT = meta_level(mT);
+        cont = rr_continue(P.rr, unit24(x.y), dT, sdiam[lT], lT, dc, meta_level(mc), p);
         if (cont) {
             prr2 = prr * p;
             const float pagg = wT / wa;
@@ -445,6 +448,21 @@ __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, Warp
                 v = fmaf(w * pc.w, __expf(-a * (d - r)), v);
             }
         } else {
+#if SBH_SWAP_WAYS == 4
+            // four independent partial sums: four child records in flight per iteration
+            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+            int k = 0;
+            for (; k + 3 < nc; k += 4) {
+                const float4 p0 = ld_pm(T, S, f + k), p1 = ld_pm(T, S, f + k + 1);
+                const float4 p2 = ld_pm(T, S, f + k + 2), p3 = ld_pm(T, S, f + k + 3);
+                s0 += node_value<KIND>(T, S, f + k, p0, q, P.kp);
+                s1 += node_value<KIND>(T, S, f + k + 1, p1, q, P.kp);
+                s2 += node_value<KIND>(T, S, f + k + 2, p2, q, P.kp);
+                s3 += node_value<KIND>(T, S, f + k + 3, p3, q, P.kp);
+            }
+            for (; k < nc; ++k) s0 += node_value<KIND>(T, S, f + k, ld_pm(T, S, f + k), q, P.kp);
+            v = w * (((s0 + s1) + (s2 + s3)) - node_value<KIND>(T, S, node, pT, q, P.kp));
+#else
             // two independent partial sums: two child records in flight per iteration
             float s0 = 0.0f, s1 = 0.0f;
             int k = 0;
@@ -455,6 +473,7 @@ __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, Warp
             }
             if (k < nc) s0 += node_value<KIND>(T, S, f + k, ld_pm(T, S, f + k), q, P.kp);
             v = w * ((s0 + s1) - node_value<KIND>(T, S, node, pT, q, P.kp));
+#endif
         }
     }
     // lane-ordered sum over the tasks of each query

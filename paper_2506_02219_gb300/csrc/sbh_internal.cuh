@@ -106,13 +106,20 @@ __device__ __forceinline__ float dist_rn(float px, float py, float pz, float3 q)
     return __fsqrt_rn(s);
 }
 
-// Eq. 5: p = min(1, max(1, beta~_T) / beta~_c), beta~ = ||q - p~|| / |B|
-__device__ __forceinline__ float rr_prob_rn(float dT, float diamT, float dc, float diamc)
+// Eq. 5 for the step from node T into its child c with the draw u: continue iff u < p,
+// p = min(1, max(1, beta~_T) / beta~_c), beta~ = ||q - p~|| / |B|. The child's cell is exactly
+// 4^-(l_c - l_T) times T's, so p = min(1, X / d_c) with X = max(d_T, |B_T|) 4^-(l_c - l_T) (exact),
+// and u < p is u d_c < X, whose sign one FMA gives exactly. rr = 1: p = 1; rr = 2: p = 1/2. On a
+// continue p gets the factor of p_rr, fl(X / d_c) capped at 1.
+__device__ __forceinline__ bool rr_continue(int rr, float u, float dT, float BT, uint32_t lT, float dc, uint32_t lc,
+                                            float& p)
 {
-    const float bt = __fdiv_rn(dT, diamT);
-    const float bc = __fdiv_rn(dc, diamc);
-    const float r = __fdiv_rn(fmaxf(bt, 1.0f), bc);  // bc == 0 -> +inf -> 1
-    return fminf(r, 1.0f);
+    if (rr == 1) { p = 1.0f; return true; }
+    if (rr == 2) { p = 0.5f; return u < 0.5f; }
+    const float X = fmaxf(dT, BT) * __int_as_float((127 - 2 * (int)(lc - lT)) << 23);
+    if (!(fmaf(u, dc, -X) < 0.0f)) return false;
+    p = dc > X ? __fdiv_rn(X, dc) : 1.0f;
+    return true;
 }
 
 // ----------------------------------------------------------------------------------------------

@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(256) k_visit(TreeView T, const float* __restri
                 const float4 pc = __ldg(&T.pm[c]);
                 const uint32_t mc = __ldg(&T.meta[c]);
                 const float dc = dist_rn(pc.x, pc.y, pc.z, q);
-                const float p = rr_prob_rn(dT, diam[meta_level(mT)], dc, diam[meta_level(mc)]);
-                if (unit24(x.y) >= p) break;
+                float p;
+                if (!rr_continue(0, unit24(x.y), dT, diam[meta_level(mT)], meta_level(mT), dc, meta_level(mc), p)) break;
                 node = c;
                 mT = mc;
                 dT = dc;

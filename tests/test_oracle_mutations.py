@@ -14,7 +14,11 @@ MUTATIONS = {
         "double pagg = p_in(t, T, a, sampling);\n                    prr",
         "double pagg = p_in(t, c, a, sampling);\n                    prr"),
     "swap with the wrong sign": ("return s - node_term(t, k, v, q);", "return node_term(t, k, v, q) - s;"),
-    "inverted roulette ratio": ("float r = num / bc;", "float r = bc / num;"),
+    "roulette threshold at the node's cell size": (
+        "float X = ldexpf(dv > bv ? dv : bv, -(t->bits / 3) * (t->level[c] - t->level[v]));",
+        "float X = dv > bv ? dv : bv;"),
+    "roulette continues when the draw is above p": ("if (!((double)u * (double)dc < (double)X)) return 0;",
+                                                    "if ((double)u * (double)dc < (double)X) return 0;"),
     "p(K >= k) missing the current step": (
         "prr *= (double)p;\n                    Fa += delta / (pagg * prr);",
         "Fa += delta / (pagg * prr);\n                    prr *= (double)p;"),
