@@ -192,7 +192,8 @@ def source_hash(paths):
     return h.hexdigest()[:16]
 
 
-EVAL_SOURCES = ["paper_2506_02219_gb300/csrc/sbh_eval_batched.cu", "paper_2506_02219_gb300/csrc/sbh_internal.cuh"]
+EVAL_SOURCES = ["paper_2506_02219_gb300/csrc/sbh_eval_batched.cu", "paper_2506_02219_gb300/csrc/sbh_internal.cuh",
+                "paper_2506_02219_gb300/csrc/sbh_learned.cuh"]
 
 
 def profiled_traffic(workload: str):
@@ -459,15 +460,15 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
         return best
 
     best = bh_time_at(err_s)
-    learned = learned_proposal(sbh, wl, tree, Q, idx, ref, seed, kk, timed) if LEARNED_NEAR > 0 else None
-    if learned is not None:
-        variants["learned_proposal"] = learned
-        # the mass-proportional estimator's time at the learned proposal's error, from its S = 1, 2, 4 rows
-        mass_pts = [(err_s, eval_ms)] + [(v["median_rel_err"], v["ms"]) for v in extra.values()]
+    # the mass-proportional estimator's time at a given error, from its S = 1 .. 4 rows
+    mass_pts = [(err_s, eval_ms)] + [(v["median_rel_err"], v["ms"]) for v in extra.values()]
+    for near in LEARNED_NEARS:
+        learned = learned_proposal(sbh, wl, tree, Q, idx, ref, seed, kk, timed, near)
         t_mass, extrap_m = interp_loglog(learned["median_rel_err"], [p[0] for p in mass_pts], [p[1] for p in mass_pts])
         learned["mass_ms_at_equal_error"] = t_mass
         learned["mass_extrapolated"] = extrap_m
         learned["speedup_vs_mass"] = t_mass / learned["ms"]
+        variants[f"learned_proposal_near{near:g}"] = learned
     for v in list(extra.values()) + list(variants.values()):
         t_bh, extrap, _ = bh_time_at(v["median_rel_err"])
         v["bh_ms_at_equal_error"] = t_bh
@@ -480,10 +481,10 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
             "time_basis": "evaluation kernels only, trees prebuilt (the paper excludes building)"}
 
 
-LEARNED_NEAR = 0.5  # gate of the learned proposal in cell diagonals (0 = skip the learned row)
+LEARNED_NEARS = (0.25, 0.5, 1.0)  # gates of the learned proposal, in cell diagonals
 
 
-def learned_proposal(sbh, wl, tree, Q, idx, ref, seed, kk, timed):
+def learned_proposal(sbh, wl, tree, Q, idx, ref, seed, kk, timed, near):
     """Train the learned child proposal on 1024 random queries in the sources' bounding box (the
     residuals the estimator's own paths meet there), then time it at S = 1 on the full query set."""
     import torch
@@ -492,13 +493,12 @@ def learned_proposal(sbh, wl, tree, Q, idx, ref, seed, kk, timed):
     net = sbh.sbh_mlp_create(1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = sbh.sbh_mlp_train(net, tree, torch.from_numpy(qt).to(Q.device), near=LEARNED_NEAR, steps=300, lr=3e-3,
-                               **kk)
+    losses = sbh.sbh_mlp_train(net, tree, torch.from_numpy(qt).to(Q.device), near=near, steps=300, lr=3e-3, **kk)
     train_s = time.perf_counter() - t0
-    out = sbh.sbh_eval_learned(tree, net, Q, seed=seed, near=LEARNED_NEAR, **kk)
-    ms = timed(lambda: sbh.sbh_eval_learned(tree, net, Q, seed=seed, near=LEARNED_NEAR, out=out, **kk), 2)
+    out = sbh.sbh_eval_learned(tree, net, Q, seed=seed, near=near, **kk)
+    ms = timed(lambda: sbh.sbh_eval_learned(tree, net, Q, seed=seed, near=near, out=out, **kk), 2)
     err = float(np.median(rel_error(wl.kernel, out[idx].cpu().numpy(), ref)))
-    return {"ms": ms, "median_rel_err": err, "near": LEARNED_NEAR, "train_s": train_s,
+    return {"ms": ms, "median_rel_err": err, "near": near, "train_s": train_s,
             "train": {"queries": 1024, "adam_steps": 300, "lr": 3e-3, "loss_first": float(losses[0]),
                       "loss_last": float(losses[-1])},
             "scorer": "tensor cores (mma.sync m16n8k16, FP16 operands, FP32 accumulation)"}

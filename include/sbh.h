@@ -198,6 +198,12 @@ SBH_API sbh_status sbh_mlp_create(uint64_t seed, void* stream, sbh_mlp** out);
  * adam_step (may be NULL) receives the number of training steps taken, for resuming. */
 SBH_API sbh_status sbh_mlp_set_weights(sbh_mlp* net, const float* host_weights, void* stream);
 SBH_API sbh_status sbh_mlp_get_weights(const sbh_mlp* net, float* host_weights, int64_t* adam_step, void* stream);
+/* The whole training state, for checkpoints: host [3 * SBH_MLP_PARAMS] FP32 = the master weights,
+ * then Adam's first and second moment estimates, and the number of Adam steps taken. Restoring it
+ * and training on the same queries continues the same optimisation (the training sets come from a
+ * fixed random stream). Synchronise. */
+SBH_API sbh_status sbh_mlp_get_state(const sbh_mlp* net, float* host_state, int64_t* adam_step, void* stream);
+SBH_API sbh_status sbh_mlp_set_state(sbh_mlp* net, const float* host_state, int64_t adam_step, void* stream);
 /* Scores of feature rows (device [n][6] -> device [n]) with the estimator's tensor-core scorer
  * (FP16 features, weights and hidden activations; FP32 accumulation). */
 SBH_API sbh_status sbh_mlp_scores(const sbh_mlp* net, const float* feats, int64_t n, float* scores, void* stream);

@@ -109,6 +109,8 @@ def load_library():
         lib.sbh_mlp_set_weights.argtypes = [P, P, P]
         lib.sbh_mlp_get_weights.argtypes = [P, P, P, P]
         lib.sbh_mlp_scores.argtypes = [P, P, i64, P, P]
+        lib.sbh_mlp_get_state.argtypes = [P, P, P, P]
+        lib.sbh_mlp_set_state.argtypes = [P, P, i64, P]
         lib.sbh_mlp_loss_grad.argtypes = [P, P, P, P, i64, P, P, P]
         lib.sbh_mlp_dataset.argtypes = [P, P, _Kernel, P, P, P, i64, P, P, P]
         lib.sbh_mlp_train.argtypes = [P, P, P, i64, _Kernel, C.c_float, i32, C.c_float, P, P]
@@ -123,7 +125,7 @@ def load_library():
         lib.sbh_mlp_free.restype = None
         for f in ("sbh_build", "sbh_eval", "sbh_eval_count", "sbh_eval_grad", "sbh_eval_bh", "sbh_eval_brute",
                   "sbh_tree_info", "sbh_tree_export", "sbh_mlp_create", "sbh_mlp_set_weights",
-                  "sbh_mlp_get_weights", "sbh_mlp_scores", "sbh_mlp_loss_grad", "sbh_mlp_dataset", "sbh_mlp_train",
+                  "sbh_mlp_get_weights", "sbh_mlp_get_state", "sbh_mlp_set_state", "sbh_mlp_scores", "sbh_mlp_loss_grad", "sbh_mlp_dataset", "sbh_mlp_train",
                   "sbh_eval_learned"):
             getattr(lib, f).restype = i32
         _lib = lib
@@ -495,6 +497,45 @@ def sbh_mlp_get_weights(net: Mlp, stream=None):
     _check(load_library().sbh_mlp_get_weights(net.handle, w.ctypes.data_as(C.c_void_p), C.byref(step),
                                               _stream(stream)))
     return w, int(step.value)
+
+
+def sbh_mlp_get_state(net: Mlp, stream=None) -> dict:
+    """Training state for a checkpoint: {"weights", "adam_m", "adam_v"} (numpy FP32) and "adam_step"."""
+    import numpy as np
+    st = np.empty(3 * MLP_PARAMS, dtype=np.float32)
+    step = C.c_int64(0)
+    _check(load_library().sbh_mlp_get_state(net.handle, st.ctypes.data_as(C.c_void_p), C.byref(step),
+                                            _stream(stream)))
+    return {"weights": st[:MLP_PARAMS].copy(), "adam_m": st[MLP_PARAMS:2 * MLP_PARAMS].copy(),
+            "adam_v": st[2 * MLP_PARAMS:].copy(), "adam_step": int(step.value)}
+
+
+def sbh_mlp_set_state(net: Mlp, state: dict, stream=None) -> None:
+    """Restore a state from sbh_mlp_get_state."""
+    import numpy as np
+    st = np.ascontiguousarray(np.concatenate([np.asarray(state[k], np.float32).reshape(-1)
+                                              for k in ("weights", "adam_m", "adam_v")]))
+    if st.size != 3 * MLP_PARAMS:
+        raise ValueError("state arrays must hold MLP_PARAMS values each")
+    _check(load_library().sbh_mlp_set_state(net.handle, st.ctypes.data_as(C.c_void_p), int(state["adam_step"]),
+                                            _stream(stream)))
+
+
+def save_mlp(net: Mlp, path: str) -> None:
+    """Write the training state to an .npz checkpoint."""
+    import numpy as np
+    np.savez(path, **sbh_mlp_get_state(net))
+
+
+def load_mlp(path: str, stream=None) -> Mlp:
+    """A network restored from an .npz checkpoint written by save_mlp."""
+    import numpy as np
+    with np.load(path) as z:
+        state = {k: z[k] for k in ("weights", "adam_m", "adam_v")}
+        state["adam_step"] = int(z["adam_step"])
+    net = sbh_mlp_create(0, stream)
+    sbh_mlp_set_state(net, state, stream)
+    return net
 
 
 def sbh_mlp_scores(net: Mlp, feats, out=None, stream=None):

@@ -413,6 +413,37 @@ sbh_status sbh_mlp_get_weights(const sbh_mlp* net, float* host_weights, int64_t*
     return SBH_OK;
 }
 
+sbh_status sbh_mlp_get_state(const sbh_mlp* net, float* host_state, int64_t* adam_step, void* stream)
+{
+    g_err[0] = 0;
+    if (!net || !host_state || !adam_step) return fail(SBH_EINVAL, "net, state and step must be non-NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t b = sbh::kMlpParams * sizeof(float);
+    cudaError_t e = cudaMemcpyAsync(host_state, net->M.w, b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_state + sbh::kMlpParams, net->M.m, b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_state + 2 * sbh::kMlpParams, net->M.v, b, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_mlp_get_state");
+    *adam_step = net->M.step;
+    return SBH_OK;
+}
+
+sbh_status sbh_mlp_set_state(sbh_mlp* net, const float* host_state, int64_t adam_step, void* stream)
+{
+    g_err[0] = 0;
+    if (!net || !host_state || adam_step < 0) return fail(SBH_EINVAL, "net and state must be non-NULL, step >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t b = sbh::kMlpParams * sizeof(float);
+    cudaError_t e = cudaMemcpyAsync(net->M.w, host_state, b, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(net->M.m, host_state + sbh::kMlpParams, b, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(net->M.v, host_state + 2 * sbh::kMlpParams, b, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = sbh::mlp_sync_half(net->M, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_mlp_set_state");
+    net->M.step = adam_step;
+    return SBH_OK;
+}
+
 sbh_status sbh_mlp_scores(const sbh_mlp* net, const float* feats, int64_t n, float* scores, void* stream)
 {
     g_err[0] = 0;

@@ -185,7 +185,7 @@ struct Params {
 // the last row taking [cum_{r-1}, 1): exactly one row of each decision is picked, and its
 // probability is the width of its interval.
 template <int KIND>
-__device__ __noinline__ void learned_picks(const Params& P, const Stage& S, const float* sdiam, unsigned gm,
+__device__ __forceinline__ void learned_picks(const Params& P, const Stage& S, const float* sdiam, unsigned gm,
                                            bool gated, float3 q, float4 pT, float BT, int32_t f, int nc, float u,
                                            int32_t& child, float& prob)
 {
@@ -340,7 +340,7 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
         const unsigned gm = __ballot_sync(0xFFFFFFFFu, gated);
         if (valid && !gated) {
             child = f + pick_child(T, S, node, f, nc, x.x, 0);
-            pick_prob = ld_pm(T, S, child).w / pT.w;
+            pick_prob = -pT.w;  // a mass pick: its probability m_c / m_T is formed on a continue
         }
         if (gm) learned_picks<KIND>(P, S, sdiam, gm, gated, q, pT, BT, f, nc, unit24(x.x), child, pick_prob);
     } else {
@@ -357,7 +357,7 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
             prr2 = prr * p;
             const float pagg = wT / wa;
             w = 1.0f / (pagg * prr2) / (float)P.S;
-            if constexpr (LEARNED) wc = wT * pick_prob;
+            if constexpr (LEARNED) wc = wT * (pick_prob < 0.0f ? pc.w / -pick_prob : pick_prob);
             else wc = P.sampling ? (float)(__ldg(&T.ne[child]) - __ldg(&T.nb[child])) : pc.w;
             // a path that reaches a source point stops there: no decision task for it (levels
             // strictly increase, so depth < kMaxDepth always holds; the test only guards a damaged tree)

@@ -205,20 +205,24 @@ __global__ void k_dataset(TreeView T, const float4* __restrict__ spw, const floa
 
 // ------------------------------------------------------------------------------------------------
 // loss and gradient: mean over sets of the cross-entropy between softmax(scores) and the set's
-// normalised targets. One warp per set, lane i = hidden unit i of both layers; per-lane partial
-// gradients (its rows of W1 and W2 and its biases) are added to the global gradient at the end.
+// normalised targets. One warp per set, lane i = hidden unit i of both layers. Each warp keeps its
+// partial gradient (per lane: its rows of W1 and W2 and its biases), the block adds its warps'
+// partials in warp order and writes one row per block; k_sum_blocks adds the rows in block order.
+// No atomics: the gradient, and so the whole training, is the same bit for bit on every run.
 // ------------------------------------------------------------------------------------------------
 constexpr int kTrainWarps = 4;
+constexpr int kTrainBlocksMax = 152 * 8;
+constexpr int kPartStride = kMlpParams + 1;  // a block's row: the gradient, then its loss
 
 __global__ void __launch_bounds__(32 * kTrainWarps) k_loss_grad(const float* __restrict__ wg,
                                                                const float* __restrict__ feats,
                                                                const float* __restrict__ targets,
                                                                const int64_t* __restrict__ off, int64_t n_sets,
-                                                               float inv_sets, float* __restrict__ grad,
-                                                               float* __restrict__ loss)
+                                                               float inv_sets, float* __restrict__ part)
 {
     __shared__ float w[kMlpParams];
     __shared__ float sc[kTrainWarps][kMaxLearnedChildren];
+    __shared__ float wpart[kTrainWarps][kPartStride];
     for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) w[i] = wg[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -281,15 +285,34 @@ __global__ void __launch_bounds__(32 * kTrainWarps) k_loss_grad(const float* __r
         }
         __syncwarp();
     }
-    for (int k = 0; k < kIn; ++k) atomicAdd(&grad[oW1 + lane * kIn + k], gW1[k]);
-    atomicAdd(&grad[ob1 + lane], gb1);
-    for (int k = 0; k < kH; ++k) atomicAdd(&grad[oW2 + lane * kH + k], gW2[k]);
-    atomicAdd(&grad[ob2 + lane], gb2);
-    atomicAdd(&grad[ow3 + lane], gw3);
+    float* wp = wpart[warp];
+    for (int k = 0; k < kIn; ++k) wp[oW1 + lane * kIn + k] = gW1[k];
+    wp[ob1 + lane] = gb1;
+    for (int k = 0; k < kH; ++k) wp[oW2 + lane * kH + k] = gW2[k];
+    wp[ob2 + lane] = gb2;
+    wp[ow3 + lane] = gw3;
     if (lane == 0) {
-        atomicAdd(&grad[ob3], gb3);
-        atomicAdd(loss, lsum * inv_sets);
+        wp[ob3] = gb3;
+        wp[kMlpParams] = lsum * inv_sets;
     }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kPartStride; i += blockDim.x) {
+        float t = 0.0f;
+        for (int v = 0; v < kTrainWarps; ++v) t += wpart[v][i];
+        part[(int64_t)blockIdx.x * kPartStride + i] = t;
+    }
+}
+
+// grad[i] = sum over blocks b (in order) of part[b][i]; loss likewise from the last column
+__global__ void k_sum_blocks(const float* __restrict__ part, int blocks, float* __restrict__ grad,
+                             float* __restrict__ loss)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kPartStride) return;
+    float t = 0.0f;
+    for (int b = 0; b < blocks; ++b) t += part[(int64_t)b * kPartStride + i];
+    if (i < kMlpParams) grad[i] = t;
+    else *loss = t;
 }
 
 __global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
@@ -326,6 +349,7 @@ cudaError_t mlp_alloc(MlpState& M, cudaStream_t s)
     if (e == cudaSuccess) e = dalloc((void**)&M.v, kMlpParams * sizeof(float), s);
     if (e == cudaSuccess) e = dalloc((void**)&M.grad, kMlpParams * sizeof(float), s);
     if (e == cudaSuccess) e = dalloc((void**)&M.loss, sizeof(float), s);
+    if (e == cudaSuccess) e = dalloc((void**)&M.part, (size_t)kTrainBlocksMax * kPartStride * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(M.m, 0, kMlpParams * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(M.v, 0, kMlpParams * sizeof(float), s);
     return e;
@@ -334,6 +358,7 @@ cudaError_t mlp_alloc(MlpState& M, cudaStream_t s)
 void mlp_release(MlpState& M, cudaStream_t s)
 {
     dfree(M.w, s); dfree(M.wh, s); dfree(M.m, s); dfree(M.v, s); dfree(M.grad, s); dfree(M.loss, s);
+    dfree(M.part, s);
     M = MlpState();
 }
 
@@ -357,13 +382,17 @@ cudaError_t mlp_scores(const MlpState& M, const float* feats, int64_t n, float* 
 cudaError_t mlp_loss_grad(MlpState& M, const float* feats, const float* targets, const int64_t* off, int64_t n_sets,
                           cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(M.grad, 0, kMlpParams * sizeof(float), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(M.loss, 0, sizeof(float), s);
-    if (e != cudaSuccess || n_sets <= 0) return e;
+    if (n_sets <= 0) {
+        cudaError_t e = cudaMemsetAsync(M.grad, 0, kMlpParams * sizeof(float), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(M.loss, 0, sizeof(float), s);
+        return e;
+    }
     int64_t blocks = (n_sets + kTrainWarps - 1) / kTrainWarps;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > kTrainBlocksMax) blocks = kTrainBlocksMax;
     k_loss_grad<<<(unsigned)blocks, 32 * kTrainWarps, 0, s>>>(M.w, feats, targets, off, n_sets, 1.0f / (float)n_sets,
-                                                             M.grad, M.loss);
+                                                             M.part);
+    note_launch();
+    k_sum_blocks<<<(kPartStride + 255) / 256, 256, 0, s>>>(M.part, (int)blocks, M.grad, M.loss);
     note_launch();
     return cudaGetLastError();
 }

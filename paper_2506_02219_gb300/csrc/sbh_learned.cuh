@@ -290,6 +290,7 @@ struct MlpState {
     float* v = nullptr;
     float* grad = nullptr;
     float* loss = nullptr;
+    float* part = nullptr;  // per-block partial gradients of the last loss evaluation
     int64_t step = 0;
 };
 

@@ -189,3 +189,24 @@ def test_training_reduces_variance_on_held_out_queries(sbh, oracle_mod, kind):
             v_learn = _variance(sbh, t, net, Q, kind, rr, 256, near)
             print(kind, "near", near, "rr", rr, "variance learned / mass", v_learn.sum() / v_mass.sum())
             assert v_learn.sum() < (0.7 if rr == 1 else 1.0) * v_mass.sum(), (near, rr, v_learn.sum(), v_mass.sum())
+
+
+def test_checkpoint_resumes_training(sbh, oracle_mod, tmp_path):
+    # 60 steps, checkpoint, 60 more on a restored copy == 120 steps straight, bit for bit (the
+    # training sets come from a fixed stream and the gradient is summed in a fixed order)
+    pts, w, nrm, q = _shapes(6000, 128, 45, "coulomb")
+    t = sbh.sbh_build(dev(pts), dev(w), dev(nrm))
+    Q = dev(q)
+    a = sbh.sbh_mlp_create(4)
+    sbh.sbh_mlp_train(a, t, Q, kernel="coulomb", near=2.0, steps=120, lr=3e-3)
+    b = sbh.sbh_mlp_create(4)
+    sbh.sbh_mlp_train(b, t, Q, kernel="coulomb", near=2.0, steps=60, lr=3e-3)
+    path = str(tmp_path / "ckpt.npz")
+    sbh.save_mlp(b, path)
+    c = sbh.load_mlp(path)
+    assert sbh.sbh_mlp_get_state(c)["adam_step"] == 60
+    sbh.sbh_mlp_train(c, t, Q, kernel="coulomb", near=2.0, steps=60, lr=3e-3)
+    wa, sa = sbh.sbh_mlp_get_weights(a)
+    wc, sc = sbh.sbh_mlp_get_weights(c)
+    assert sa == sc == 120
+    assert np.array_equal(wc, wa)
