@@ -184,6 +184,18 @@ def interp_loglog(x_target, xs, ys):
     return float(np.exp(np.interp(t, lx, ly))), False
 
 
+def error_stats(kind, est, ref):
+    """Absolute and relative errors (relative as in rel_error) of an estimate: mean, median, max."""
+    est = np.asarray(est, np.float64)
+    ref = np.asarray(ref, np.float64)
+    ok = np.isfinite(est)
+    a = np.abs(est - ref)[ok]
+    r = rel_error(kind, est, ref)[ok]
+    return {"abs": {"mean": float(a.mean()), "median": float(np.median(a)), "max": float(a.max())},
+            "rel": {"mean": float(r.mean()), "median": float(np.median(r)), "max": float(r.max())},
+            "non_finite": int((~ok).sum()), "queries": int(est.size)}
+
+
 def source_hash(paths):
     h = hashlib.sha256()
     for p in paths:
@@ -408,6 +420,7 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
     ref = sbh.sbh_eval_brute(P, M, Qs, normals=N, fp64_accum=True, **kk).cpu().numpy()
     out = sbh.sbh_eval(tree, Q, samples_per_subdomain=S, seed=seed, **kk)
     err_s = float(np.median(rel_error(wl.kernel, out[idx].cpu().numpy(), ref)))
+    stats_s = error_stats(wl.kernel, out[idx].cpu().numpy(), ref)
 
     def timed(fn, reps=3):
         fn()
@@ -473,7 +486,8 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
         t_bh, extrap, _ = bh_time_at(v["median_rel_err"])
         v["bh_ms_at_equal_error"] = t_bh
         v["speedup_vs_bh"] = t_bh / v["ms"]
-    return {"stochastic": {"S": S, "ms": eval_ms, "median_rel_err": err_s, **extra}, "variants": variants,
+    return {"stochastic": {"S": S, "ms": eval_ms, "median_rel_err": err_s, "errors": stats_s, **extra},
+            "variants": variants,
             "bh_sweep": sweep, "bh_tree_build_ms": bh_build_ms,
             "bh_ms_at_equal_error": best[0], "bh_warp_vote": best[2], "extrapolated": best[1],
             "speedup_vs_bh_at_equal_median_error": best[0] / eval_ms,
@@ -553,21 +567,67 @@ def batched_sets(rank: int = 0, n_sets: int = 64):
     return sets
 
 
+BATCHED_KERNEL = "smoothdist"  # smooth distance (alpha = 200, unit weights) over the batched sets
+
+
+def batched_adjoint(sbh, p, w, q, tree, S, seed, dev):
+    """The adjoint on one set: time of sbh_eval_grad (value and d/dq under the estimator's stream),
+    its median relative error against the GPU brute-force gradient (FP64 accumulation), and its
+    median relative gap to central differences (h = 1e-4) of the estimate with the roulette off,
+    where the frozen-path derivative is the derivative of the estimate."""
+    import torch
+    P, M, Q = (torch.from_numpy(x).to(dev) for x in (p, w, q))
+    kk = dict(kernel=BATCHED_KERNEL, alpha=200.0)
+    out, grad = sbh.sbh_eval_grad(tree, Q, samples_per_subdomain=S, seed=seed, **kk)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        sbh.sbh_eval_grad(tree, Q, samples_per_subdomain=S, seed=seed, out=out, grad=grad, **kk)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / 5
+    _, gref = sbh.sbh_eval_brute_grad(P, M, Q, **kk)
+    g, gr = grad.double().cpu().numpy(), gref.double().cpu().numpy()
+    ok = np.all(np.isfinite(g), axis=1) & np.all(np.isfinite(gr), axis=1)
+    err = np.linalg.norm(g - gr, axis=1)[ok] / np.maximum(np.linalg.norm(gr, axis=1)[ok], 1e-30)
+    # central differences of the estimate along each axis, roulette off
+    o = sbh.eval_opts(rr=1)
+    _, g1 = sbh.sbh_eval_grad(tree, Q, samples_per_subdomain=S, seed=seed, opts=o, **kk)
+    h = 1e-4
+    fd = torch.empty_like(g1)
+    for a in range(3):
+        dq = torch.zeros(3, device=dev)
+        dq[a] = h
+        fp = sbh.sbh_eval(tree, (Q + dq).contiguous(), samples_per_subdomain=S, seed=seed, opts=o, **kk)
+        fm = sbh.sbh_eval(tree, (Q - dq).contiguous(), samples_per_subdomain=S, seed=seed, opts=o, **kk)
+        fd[:, a] = (fp.double() - fm.double()).float() / (2 * h)
+    g1n, fdn = g1.double().cpu().numpy(), fd.double().cpu().numpy()
+    ok1 = np.all(np.isfinite(g1n), axis=1) & np.all(np.isfinite(fdn), axis=1)
+    gap = np.linalg.norm(g1n - fdn, axis=1)[ok1] / np.maximum(np.linalg.norm(g1n, axis=1)[ok1], 1e-30)
+    return {"set_sources": int(p.shape[0]), "set_queries": int(q.shape[0]), "S": S, "ms": ms,
+            "queries_per_s": q.shape[0] / (ms / 1e3),
+            "median_rel_err_vs_brute_grad": float(np.median(err)), "finite_fraction": float(ok.mean()),
+            "median_rel_gap_vs_central_fd_roulette_off": float(np.median(gap)), "fd_h": h}
+
+
 def run_batched(args):
-    """Many independent source/query sets in one persistent, graph-captured launch; S and leaf size
-    from the autotuner (largest set, target = the median error of S = 1, leaf 1). A step is one replay
-    of the captured launch (the trees are built once, their build time is reported)."""
+    """Many independent source/query sets (smooth distance) in one persistent, graph-captured launch;
+    S and leaf size from the autotuner (on the largest set, the most efficient: smallest time x
+    error^2). A step is one replay of the captured launch (the trees are built once, their build
+    time is reported). Then the adjoint on the largest set against the brute-force gradient and
+    finite differences."""
     import torch
     import paper_2506_02219_gb300 as sbh
     from paper_2506_02219_gb300 import _build, autotune
     _build.build()
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
-    sets = batched_sets()
+    sets = [(p, np.ones_like(w), q) for p, w, q in batched_sets()]
     big = max(range(len(sets)), key=lambda i: sets[i][0].shape[0])
     p, w, q = sets[big]
     tune = autotune.autotune(torch.from_numpy(p).to(dev), torch.from_numpy(w).to(dev), torch.from_numpy(q).to(dev),
-                             "coulomb", leaf_sizes=(1, 2, 4), samples=(1, 2), schedules=(0,))
+                             BATCHED_KERNEL, leaf_sizes=(1, 2, 4), samples=(1, 2), schedules=(0,))
     leaf, S = tune["best"]["leaf_size"], tune["best"]["S"]
     t0 = time.perf_counter()
     trees, Qs = [], []
@@ -576,7 +636,7 @@ def run_batched(args):
         Qs.append(torch.from_numpy(q).to(dev))
     torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
-    plan = sbh.sbh_multi_plan_create(trees, Qs, "coulomb", S, seed=0x5BA7)
+    plan = sbh.sbh_multi_plan_create(trees, Qs, BATCHED_KERNEL, S, seed=0x5BA7)
     graph = sbh.capture_multi(plan)
     for _ in range(args.warmup):
         graph.replay()
@@ -591,17 +651,21 @@ def run_batched(args):
     e1.record()
     torch.cuda.synchronize()
     clk = clocks.stop()
+    # graph replays launch the captured kernels without passing through the library's counter
+    launches = sbh.sbh_kernel_launches() - launches0 + args.steps * graph.sbh_kernels
     ms = e0.elapsed_time(e1) / args.steps
     total_q = sum(int(q.shape[0]) for q in Qs)
+    adj = batched_adjoint(sbh, *sets[big], trees[big], S, 0x5BA7, dev)
     print(json.dumps({"metric": METRIC, "value": total_q / (ms / 1e3), "unit": "queries/s", "n_gpus": 1,
                       "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                       "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                      "config": {"workload": "batched_64sets_coulomb", "sets": len(sets),
+                      "config": {"workload": f"batched_64sets_{BATCHED_KERNEL}", "sets": len(sets),
                                  "sources": int(sum(s[0].shape[0] for s in sets)), "queries": total_q,
+                                 "kernel": BATCHED_KERNEL, "alpha": 200.0,
                                  "samples_per_subdomain": S, "leaf_size": leaf,
                                  "step": "one replay of the graph-captured multi-set launch"},
-                      "build_s_all_sets": build_s, "autotune": tune, "clocks": clk,
-                      "gpu_launches": sbh.sbh_kernel_launches() - launches0}), flush=True)
+                      "build_s_all_sets": build_s, "autotune": tune, "adjoint": adj, "clocks": clk,
+                      "gpu_launches": launches}), flush=True)
 
 
 def main(argv=None):

@@ -272,6 +272,13 @@ SBH_API sbh_status sbh_eval_brute(const float* points, const float* weights, con
                           const float* queries, int64_t nq, sbh_kernel kernel, int32_t fp64_accum,
                           float* out, void* stream);
 
+/* The exact sum and its gradient with respect to the query position (tiled brute force, FP32
+ * per-tile partials added in FP64), in the conventions of sbh_eval_grad: out [nq] is F (the
+ * distance d for the smooth distance), grad [nq][3] its gradient (grad d = -grad F / (alpha F)). */
+SBH_API sbh_status sbh_eval_brute_grad(const float* points, const float* weights, const float* normals, int64_t n,
+                                       const float* queries, int64_t nq, sbh_kernel kernel, float* out, float* grad,
+                                       void* stream);
+
 /* Tree summary (host struct). Synchronises the tree's build stream. which: 0 or 1 (see above);
  * SBH_EUNSUPPORTED when the 8-ary tree has not been built yet. */
 SBH_API sbh_status sbh_tree_info(const sbh_tree* tree, int32_t which, sbh_tree_meta* meta);

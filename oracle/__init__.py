@@ -69,7 +69,8 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = C.CDLL(build())
+        # SBHO_LIB: load a separately built copy (the sanitizer test builds one with ASan/UBSan)
+        lib = C.CDLL(os.environ.get("SBHO_LIB") or build())
         P = C.c_void_p
         i64, i32, u64 = C.c_int64, C.c_int32, C.c_uint64
         lib.sbho_philox4x32_10.argtypes = [P, P, P]

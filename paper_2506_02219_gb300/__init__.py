@@ -101,6 +101,8 @@ def load_library():
         lib.sbh_multi_plan_free.restype = None
         lib.sbh_eval_bh.argtypes = [P, P, i64, _Kernel, C.c_float, i32, P, P]
         lib.sbh_eval_brute.argtypes = [P, P, P, i64, P, i64, _Kernel, i32, P, P]
+        lib.sbh_eval_brute_grad.argtypes = [P, P, P, i64, P, i64, _Kernel, P, P, P]
+        lib.sbh_eval_brute_grad.restype = i32
         lib.sbh_tree_info.argtypes = [P, i32, C.POINTER(_Meta)]
         lib.sbh_tree_export.argtypes = [P, i32, C.POINTER(_Export)]
         lib.sbh_tree_free.argtypes = [P]
@@ -370,7 +372,8 @@ def sbh_multi_plan_free(plan: MultiPlan) -> None:
 
 
 def capture_multi(plan: MultiPlan):
-    """Capture one launch of the plan into a torch.cuda.CUDAGraph; graph.replay() re-runs it."""
+    """Capture one launch of the plan into a torch.cuda.CUDAGraph; graph.replay() re-runs it.
+    graph.sbh_kernels is the number of the library's kernels one replay launches."""
     import torch
     s = torch.cuda.Stream()
     s.wait_stream(torch.cuda.current_stream())
@@ -378,8 +381,10 @@ def capture_multi(plan: MultiPlan):
         sbh_multi_plan_launch(plan)
     torch.cuda.current_stream().wait_stream(s)
     g = torch.cuda.CUDAGraph()
+    n0 = sbh_kernel_launches()
     with torch.cuda.graph(g):
         sbh_multi_plan_launch(plan)
+    g.sbh_kernels = sbh_kernel_launches() - n0
     return g
 
 
@@ -416,6 +421,24 @@ def sbh_eval_brute(points, weights, queries, kernel="coulomb", normals=None, fp6
                               _dev(normals, "normals", 3, allow_none=True), n, _dev(queries, "queries", 3), nq, k,
                               int(bool(fp64_accum)), _dev(out, "out"), _stream(stream)))
     return out
+
+
+def sbh_eval_brute_grad(points, weights, queries, kernel="coulomb", normals=None, out=None, grad=None, stream=None,
+                        softening: float = 1e-3, alpha: float = 200.0, affine=(0.0, 0.0, 0.0)):
+    """Exact sum and its query gradient by tiled brute force (FP64 accumulation), in the
+    conventions of sbh_eval_grad; returns (out [nq], grad [nq, 3])."""
+    torch = _torch()
+    n, nq = int(points.shape[0]), int(queries.shape[0])
+    if out is None:
+        out = torch.empty(nq, dtype=torch.float32, device=queries.device)
+    if grad is None:
+        grad = torch.empty((nq, 3), dtype=torch.float32, device=queries.device)
+    k = _kernel_arg(kernel, softening, alpha, affine)
+    _check(load_library().sbh_eval_brute_grad(_dev(points, "points", 3), _dev(weights, "weights"),
+                                              _dev(normals, "normals", 3, allow_none=True), n,
+                                              _dev(queries, "queries", 3), nq, k, _dev(out, "out"),
+                                              _dev(grad, "grad", 3), _stream(stream)))
+    return out, grad
 
 
 def sbh_tree_info(tree: Tree, which: int = 0) -> dict:

@@ -691,6 +691,28 @@ sbh_status sbh_eval_brute(const float* points, const float* weights, const float
     return SBH_OK;
 }
 
+sbh_status sbh_eval_brute_grad(const float* points, const float* weights, const float* normals, int64_t n,
+                               const float* queries, int64_t nq, sbh_kernel kernel, float* out, float* grad,
+                               void* stream)
+{
+    g_err[0] = 0;
+    if (n < 0 || nq < 0) return fail(SBH_EINVAL, "n and nq must be >= 0");
+    sbh::KernelParams kp;
+    sbh_status st = check_kernel(kernel, &kp);
+    if (st != SBH_OK) return st;
+    if (nq == 0) return SBH_OK;
+    if (n > 0 && (!device_ptr(points) || !device_ptr(weights)))
+        return fail(SBH_EINVAL, "points and weights must be device memory");
+    if (kernel.kind == SBH_WINDING && n > 0 && !device_ptr(normals))
+        return fail(SBH_EINVAL, "the winding-number kernel needs normals");
+    if (!device_ptr(queries) || !device_ptr(out) || !device_ptr(grad))
+        return fail(SBH_EINVAL, "queries, out and grad must be device memory");
+    cudaError_t e = sbh::launch_brute_grad(points, weights, normals, n, queries, nq, kp, out, grad,
+                                           (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_eval_brute_grad launch");
+    return SBH_OK;
+}
+
 sbh_status sbh_tree_info(const sbh_tree* tree, int32_t which, sbh_tree_meta* meta)
 {
     g_err[0] = 0;

@@ -47,5 +47,7 @@ cudaError_t launch_bh_eval(const TreeView& T, const float* Q, int64_t nq, const 
 
 cudaError_t launch_brute(const float* P, const float* W, const float* N, int64_t n, const float* Q, int64_t nq,
                          const KernelParams& kp, int fp64_accum, float* out, cudaStream_t s);
+cudaError_t launch_brute_grad(const float* P, const float* W, const float* N, int64_t n, const float* Q, int64_t nq,
+                              const KernelParams& kp, float* out, float* grad, cudaStream_t s);
 
 }  // namespace sbh

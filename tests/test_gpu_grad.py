@@ -11,6 +11,8 @@
   finite differences.) For the smooth distance, at many samples the adjoint of d = -log(F)/alpha
   approaches the FP64 brute-force gradient.
 - torch.autograd: StochasticSum's backward is the adjoint.
+- The GPU brute-force gradient (the bench's error reference for the adjoint) against the oracle's
+  FP64 brute-force value and gradient.
 """
 import numpy as np
 import pytest
@@ -125,3 +127,20 @@ def test_autograd_backward_is_the_adjoint(sbh):
     torch.testing.assert_close(Q.grad, ref)
     val = sbh.sbh_eval(t, dev(q), "coulomb", 1, 17)
     torch.testing.assert_close(out.detach(), val, rtol=1e-5, atol=0)
+
+
+@pytest.mark.parametrize("kind", ["coulomb", "winding", "smoothdist", "affine"])
+def test_brute_gradient_matches_oracle(sbh, oracle_mod, kind):
+    """sbh_eval_brute_grad against the oracle's FP64 brute-force value and gradient: FP32 tile
+    partials added in FP64 leave errors near FP32 rounding of one tile (1e-5 of the scale)."""
+    pts, w, nrm, q = _inputs(kind, 5000, 700, 61)
+    kw = oracle_kwargs(oracle_mod, kind, alpha=30.0)
+    F = oracle_mod.brute(pts, w, q, normals=nrm, **kw)
+    G = oracle_mod.brute_grad(pts, w, q, normals=nrm, **kw)
+    out, grad = sbh.sbh_eval_brute_grad(dev(pts), dev(w), dev(q), normals=dev(nrm), **gpu_kwargs(kind, alpha=30.0))
+    out, grad = out.cpu().numpy().astype(np.float64), grad.cpu().numpy().astype(np.float64)
+    if kind == "smoothdist":  # distance and its gradient -grad F / (alpha F)
+        F, G = -np.log(F) / 30.0, -G / (30.0 * F[:, None])
+    scale = np.abs(G).max()
+    assert np.all(np.abs(grad - G) <= 1e-5 * scale + 1e-5 * np.abs(G)), np.abs(grad - G).max() / scale
+    np.testing.assert_allclose(out, F, rtol=1e-5, atol=1e-6 * np.abs(F).max())

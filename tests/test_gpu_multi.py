@@ -50,6 +50,7 @@ def test_multi_launch_replays_from_a_cuda_graph(sbh):
     plan = sbh.sbh_multi_plan_create(trees, Qs, "coulomb", 1, seed=3)
     direct = [o.clone() for o in sbh.sbh_multi_plan_launch(plan)]
     graph = sbh.capture_multi(plan)
+    assert graph.sbh_kernels == 1  # one persistent launch per replay
     for _ in range(3):
         for o in plan.outs:
             o.zero_()
