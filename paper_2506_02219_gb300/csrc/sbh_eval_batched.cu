@@ -28,6 +28,10 @@ namespace {
 #ifndef SBH_STAGE_MAX
 #define SBH_STAGE_MAX 2048
 #endif
+// most blocks launched per SM (the rest of the tiles are taken in grid-stride order)
+#ifndef SBH_GRID_BLOCKS_PER_SM
+#define SBH_GRID_BLOCKS_PER_SM 96
+#endif
 // child records in flight per lane in a swap task (2 or 4)
 #ifndef SBH_SWAP_WAYS
 #define SBH_SWAP_WAYS 2
@@ -711,7 +715,7 @@ static cudaError_t launch_batched_impl(const TreeView& T, const TreeCtrl& host_c
     P.mlpw = (const __half*)mlp_half; P.near = near; P.frag = nullptr; P.learn = nullptr;
     const int64_t tiles = (nq + 31) / 32;
     int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > 152 * SBH_GRID_BLOCKS_PER_SM) blocks = 152 * SBH_GRID_BLOCKS_PER_SM;
     // stage generations 1 and 2 (the subdomains and their children), at most kStageMax nodes
     // (half as many with the learned proposal, whose scratch takes the rest of the room)
     const int32_t lo = host_ctrl.max_depth >= 1 ? host_ctrl.depth_base[1] : 0;
