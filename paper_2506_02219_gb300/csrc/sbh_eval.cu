@@ -34,6 +34,11 @@ constexpr int kModeGrad = 1;
 constexpr int kModeEval = 2;
 constexpr int kModeLearned = 3;  // evaluation with the learned child proposal
 
+// most blocks launched per SM (the rest of the queries are taken in grid-stride order)
+#ifndef SBH_LANE_GRID_BLOCKS_PER_SM
+#define SBH_LANE_GRID_BLOCKS_PER_SM 256
+#endif
+
 // Running sum of weighted terms and of their query gradients. The smooth-distance kernel keeps
 // both in units of exp(-alpha ref), ref the smallest distance seen so far.
 template <int KIND, bool GRAD>
@@ -229,7 +234,7 @@ cudaError_t launch_lane_impl(const TreeView& T, const float* Q, int64_t nq, cons
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     const int threads = 256;
     int64_t blocks = (nq + threads - 1) / threads;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > 152 * SBH_LANE_GRID_BLOCKS_PER_SM) blocks = 152 * SBH_LANE_GRID_BLOCKS_PER_SM;
     const unsigned b = (unsigned)blocks;
     switch (kp.kind) {
     case SBH_COULOMB:
