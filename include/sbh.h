@@ -156,6 +156,20 @@ SBH_API sbh_status sbh_eval_grad(const sbh_tree* tree, const float* queries, int
                                  int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
                                  float* out, float* grad, void* stream);
 
+/* One-shot build and evaluation from HOST buffers (the call for callers without device memory
+ * of their own): points [n][3], weights [n], normals [n][3] or NULL, queries [nq][3] and out [nq] are
+ * host memory. The points go up and the tree is built (as sbh_build) while the queries go up chunk
+ * by chunk (chunk queries each, rounded up to a multiple of 32; 0 = max(2^24, nq / 4)) on a copy
+ * stream; each chunk is evaluated
+ * (as sbh_eval, with the random stream of its place in the whole set, so out equals sbh_eval on
+ * all queries bit for bit) as soon as it has landed, and its results come back on a second copy
+ * stream while the next chunk runs. Page-locked host memory lets the copies overlap; pageable
+ * memory works, without the overlap. The tree is freed before returning. Synchronises. */
+SBH_API sbh_status sbh_solve_host(const float* points, const float* weights, const float* normals, int64_t n,
+                                  int32_t leaf_size, const float* queries, int64_t nq, sbh_kernel kernel,
+                                  int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
+                                  int64_t chunk, float* out, void* stream);
+
 /* The work sbh_eval does for the same arguments, counted instead of evaluated: the same paths
  * are walked (same decisions) and no output is written. counts: device [4] unsigned 64-bit,
  * accumulated into (the caller zeroes them): [0] kernel terms evaluated (control variates, every

@@ -102,6 +102,9 @@ def load_library():
         lib.sbh_eval_bh.argtypes = [P, P, i64, _Kernel, C.c_float, i32, P, P]
         lib.sbh_eval_brute.argtypes = [P, P, P, i64, P, i64, _Kernel, i32, P, P]
         lib.sbh_eval_brute_grad.argtypes = [P, P, P, i64, P, i64, _Kernel, P, P, P]
+        lib.sbh_solve_host.argtypes = [P, P, P, i64, i32, P, i64, _Kernel, i32, C.c_uint64, C.POINTER(EvalOpts),
+                                       i64, P, P]
+        lib.sbh_solve_host.restype = i32
         lib.sbh_eval_brute_grad.restype = i32
         lib.sbh_tree_info.argtypes = [P, i32, C.POINTER(_Meta)]
         lib.sbh_tree_export.argtypes = [P, i32, C.POINTER(_Export)]
@@ -420,6 +423,46 @@ def sbh_eval_brute(points, weights, queries, kernel="coulomb", normals=None, fp6
     _check(lib.sbh_eval_brute(_dev(points, "points", 3), _dev(weights, "weights"),
                               _dev(normals, "normals", 3, allow_none=True), n, _dev(queries, "queries", 3), nq, k,
                               int(bool(fp64_accum)), _dev(out, "out"), _stream(stream)))
+    return out
+
+
+def _host(a, name, cols=None, allow_none=False):
+    """Pointer to a contiguous float32 host buffer (numpy array or CPU tensor, pinned or not)."""
+    import numpy as np
+    if a is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    torch = _torch()
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or a.dtype != torch.float32 or not a.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 CPU tensor")
+        ptr, shape = a.data_ptr(), tuple(a.shape)
+    else:
+        if not (isinstance(a, np.ndarray) and a.dtype == np.float32 and a.flags.c_contiguous):
+            raise ValueError(f"{name} must be a C-contiguous float32 numpy array")
+        ptr, shape = a.ctypes.data, a.shape
+    if cols is not None and (len(shape) != 2 or shape[1] != cols):
+        raise ValueError(f"{name} must have shape [n, {cols}]")
+    return C.c_void_p(ptr)
+
+
+def sbh_solve_host(points, weights, queries, normals=None, leaf_size: int = 1, kernel="coulomb",
+                   samples_per_subdomain: int = 1, seed: int = 0, opts: EvalOpts | None = None, chunk: int = 0,
+                   out=None, stream=None, softening: float = 1e-3, alpha: float = 200.0, affine=(0.0, 0.0, 0.0)):
+    """One-shot build and evaluation from host buffers (numpy arrays or CPU tensors; page-locked
+    memory lets the copies overlap the work); returns out (host, float32 [nq])."""
+    import numpy as np
+    n, nq = int(points.shape[0]), int(queries.shape[0])
+    if out is None:
+        out = np.empty(nq, dtype=np.float32)
+    k = _kernel_arg(kernel, softening, alpha, affine)
+    _check(load_library().sbh_solve_host(_host(points, "points", 3), _host(weights, "weights"),
+                                         _host(normals, "normals", 3, allow_none=True), n, int(leaf_size),
+                                         _host(queries, "queries", 3), nq, k, int(samples_per_subdomain),
+                                         C.c_uint64(int(seed) & (2**64 - 1)),
+                                         C.byref(opts) if opts is not None else None, int(chunk),
+                                         _host(out, "out"), _stream(stream)))
     return out
 
 

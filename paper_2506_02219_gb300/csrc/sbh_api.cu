@@ -7,7 +7,9 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <cmath>
 #include <vector>
 #include <new>
@@ -185,6 +187,114 @@ sbh_status sbh_eval(const sbh_tree* tree, const float* queries, int64_t nq, sbh_
     cudaError_t e = sbh::launch_stoch_eval(tree->t4.view(), tree->host_ctrl4, queries, nq, kp, samples_per_subdomain,
                                            seed, o, out, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "sbh_eval launch");
+    return SBH_OK;
+}
+
+namespace {
+// per-device copy streams of sbh_solve_host (created on first use, kept for the process)
+std::mutex g_copy_mutex;
+cudaStream_t g_copy_in[64], g_copy_out[64];
+
+cudaError_t copy_streams(cudaStream_t* ci, cudaStream_t* co)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_copy_mutex);
+    if (!g_copy_in[dev]) {
+        e = cudaStreamCreateWithFlags(&g_copy_in[dev], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g_copy_out[dev], cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+    }
+    *ci = g_copy_in[dev];
+    *co = g_copy_out[dev];
+    return cudaSuccess;
+}
+}  // namespace
+
+sbh_status sbh_solve_host(const float* points, const float* weights, const float* normals, int64_t n,
+                          int32_t leaf_size, const float* queries, int64_t nq, sbh_kernel kernel,
+                          int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts, int64_t chunk,
+                          float* out, void* stream)
+{
+    g_err[0] = 0;
+    if (!points || !weights || (nq > 0 && (!queries || !out))) return fail(SBH_EINVAL, "NULL buffer");
+    if (device_ptr(points) || device_ptr(weights) || (normals && device_ptr(normals)) ||
+        (nq > 0 && (device_ptr(queries) || device_ptr(out))))
+        return fail(SBH_EINVAL, "sbh_solve_host takes host buffers (use sbh_build and sbh_eval for device ones)");
+    if (nq < 0 || chunk < 0) return fail(SBH_EINVAL, "nq and chunk must be >= 0");
+    if (samples_per_subdomain < 1) return fail(SBH_EINVAL, "samples_per_subdomain must be >= 1");
+    if (n < 1 || n > kMaxPoints) return fail(SBH_EINVAL, "n = %lld outside [1, 2^28]", (long long)n);
+    sbh::KernelParams kp;
+    sbh_status st = check_kernel(kernel, &kp);
+    if (st != SBH_OK) return st;
+    if (kernel.kind == SBH_WINDING && !normals) return fail(SBH_EINVAL, "the winding-number kernel needs normals");
+    sbh_eval_opts o = {0, 0, 0, 0, 0};
+    if (opts) o = *opts;
+    if (!opts_ok(o)) return fail(SBH_EINVAL, "sbh_eval_opts out of range");
+    // each chunk adds a launch tail (~0.15 ms); uploads are overlapped with the build anyway, so
+    // only very large query sets are split (their downloads then overlap the next chunk)
+    if (chunk == 0) chunk = std::max<int64_t>(int64_t(1) << 24, (nq + 3) / 4);
+    // whole 32-query tiles: a tile's results depend on its queries only, so the chunks' tiles must
+    // be those of one launch over all queries
+    chunk = (chunk + 31) / 32 * 32;
+    const int64_t n_chunks = nq > 0 ? (nq + chunk - 1) / chunk : 0;
+    cudaStream_t s = (cudaStream_t)stream, ci = nullptr, co = nullptr;
+    cudaError_t e = copy_streams(&ci, &co);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_solve_host streams");
+    float *dP = nullptr, *dW = nullptr, *dN = nullptr, *dQ = nullptr, *dO = nullptr;
+    std::vector<cudaEvent_t> ev((size_t)(2 * n_chunks + 2), nullptr);
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = sbh::dalloc((void**)&dP, (size_t)n * 3 * sizeof(float), s);
+    if (e == cudaSuccess) e = sbh::dalloc((void**)&dW, (size_t)n * sizeof(float), s);
+    if (e == cudaSuccess && normals) e = sbh::dalloc((void**)&dN, (size_t)n * 3 * sizeof(float), s);
+    if (e == cudaSuccess && nq > 0) e = sbh::dalloc((void**)&dQ, (size_t)nq * 3 * sizeof(float), s);
+    if (e == cudaSuccess && nq > 0) e = sbh::dalloc((void**)&dO, (size_t)nq * sizeof(float), s);
+    // the queries go in chunk by chunk on the copy stream, overlapping the build
+    if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ci, ev[0], 0);
+    for (int64_t k = 0; k < n_chunks && e == cudaSuccess; ++k) {
+        const int64_t b = k * chunk, m = std::min(chunk, nq - b);
+        e = cudaMemcpyAsync(dQ + 3 * b, queries + 3 * b, (size_t)m * 3 * sizeof(float), cudaMemcpyHostToDevice, ci);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[(size_t)(1 + k)], ci);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dP, points, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dW, weights, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && normals)
+        e = cudaMemcpyAsync(dN, normals, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
+    sbh_tree* tree = nullptr;
+    if (e == cudaSuccess) {
+        st = sbh_build(dP, dW, dN, n, leaf_size, (void*)s, &tree);  // synchronises s
+        if (st != SBH_OK) {
+            cudaStreamSynchronize(ci);
+            sbh::dfree(dP, s); sbh::dfree(dW, s); sbh::dfree(dN, s); sbh::dfree(dQ, s); sbh::dfree(dO, s);
+            cudaStreamSynchronize(s);
+            for (auto& x : ev) if (x) cudaEventDestroy(x);
+            return st;
+        }
+    }
+    // evaluate each chunk as it lands; its results go out on the second copy stream
+    for (int64_t k = 0; k < n_chunks && e == cudaSuccess; ++k) {
+        const int64_t b = k * chunk, m = std::min(chunk, nq - b);
+        e = cudaStreamWaitEvent(s, ev[(size_t)(1 + k)], 0);
+        if (e == cudaSuccess)
+            e = sbh::launch_stoch_eval(tree->t4.view(), tree->host_ctrl4, dQ + 3 * b, m, kp, samples_per_subdomain,
+                                       seed, o, dO + b, s, b);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[(size_t)(1 + n_chunks + k)], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(co, ev[(size_t)(1 + n_chunks + k)], 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out + b, dO + b, (size_t)m * sizeof(float), cudaMemcpyDeviceToHost, co);
+    }
+    // everything done before the buffers go back to the pool
+    const cudaError_t e_in = cudaStreamSynchronize(ci), e_out = cudaStreamSynchronize(co);
+    if (e == cudaSuccess) e = e_in != cudaSuccess ? e_in : e_out;
+    if (tree) sbh_tree_free(tree);
+    sbh::dfree(dP, s); sbh::dfree(dW, s); sbh::dfree(dN, s); sbh::dfree(dQ, s); sbh::dfree(dO, s);
+    const cudaError_t e_s = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = e_s;
+    for (auto& x : ev) if (x) cudaEventDestroy(x);
+    if (e != cudaSuccess) return cuda_fail(e, "sbh_solve_host");
     return SBH_OK;
 }
 

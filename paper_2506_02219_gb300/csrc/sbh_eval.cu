@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                                                     KernelParams kp, int S, uint2 key, int sampling, int rr,
                                                     int coherent, int raw_sum, float* __restrict__ out,
                                                     float* __restrict__ grad, unsigned long long* __restrict__ counts,
-                                                    const __half* __restrict__ mlpw, float near)
+                                                    const __half* __restrict__ mlpw, float near, int64_t qbase)
 {
     constexpr bool COUNT = MODE == kModeCount;
     constexpr bool GRAD = MODE == kModeGrad;
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                 float ppath = 1.0f;  // learned proposal: probability of the picks so far
                 for (uint32_t depth = 0; meta_kind(mT) != kPoint && depth < (uint32_t)kMaxDepth; ++depth) {
                     const uint4 x = philox4x32_10(
-                        make_uint4(coherent ? 0u : (uint32_t)j, (uint32_t)ai, (uint32_t)s, depth), key);
+                        make_uint4(coherent ? 0u : (uint32_t)(j + qbase), (uint32_t)ai, (uint32_t)s, depth), key);
                     const int32_t f = __ldg(&T.fc[node]);
                     const int nc = (int)meta_nchild(mT);
                     int pick = 0;
@@ -228,7 +228,7 @@ template <int MODE>
 cudaError_t launch_lane_impl(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
                              uint64_t seed, const sbh_eval_opts& o, float* out, float* grad,
                              unsigned long long* counts, cudaStream_t s, const __half* mlpw = nullptr,
-                             float near = 0.0f)
+                             float near = 0.0f, int64_t qbase = 0)
 {
     if (nq <= 0) return cudaSuccess;
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
@@ -238,16 +238,16 @@ cudaError_t launch_lane_impl(const TreeView& T, const float* Q, int64_t nq, cons
     const unsigned b = (unsigned)blocks;
     switch (kp.kind) {
     case SBH_COULOMB:
-        k_stoch_eval<SBH_COULOMB, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw, near);
+        k_stoch_eval<SBH_COULOMB, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw, near, qbase);
         break;
     case SBH_WINDING:
-        k_stoch_eval<SBH_WINDING, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw, near);
+        k_stoch_eval<SBH_WINDING, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw, near, qbase);
         break;
     case SBH_SMOOTHDIST:
-        k_stoch_eval<SBH_SMOOTHDIST, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw, near);
+        k_stoch_eval<SBH_SMOOTHDIST, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw, near, qbase);
         break;
     case SBH_AFFINE:
-        k_stoch_eval<SBH_AFFINE, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw, near);
+        k_stoch_eval<SBH_AFFINE, MODE><<<b, threads, 0, s>>>(T, Q, nq, kp, S, key, o.sampling, o.rr, o.seed_mode, o.raw_sum, out, grad, counts, mlpw, near, qbase);
         break;
     default:
         return cudaErrorInvalidValue;
@@ -260,10 +260,11 @@ cudaError_t launch_lane_impl(const TreeView& T, const float* Q, int64_t nq, cons
 
 cudaError_t launch_stoch_eval(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
                               const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
-                              cudaStream_t s)
+                              cudaStream_t s, int64_t qbase)
 {
-    if (o.schedule == 1) return launch_lane_impl<kModeEval>(T, Q, nq, kp, S, seed, o, out, nullptr, nullptr, s);
-    return launch_stoch_batched(T, host_ctrl, Q, nq, kp, S, seed, o, out, s);
+    if (o.schedule == 1)
+        return launch_lane_impl<kModeEval>(T, Q, nq, kp, S, seed, o, out, nullptr, nullptr, s, nullptr, 0.0f, qbase);
+    return launch_stoch_batched(T, host_ctrl, Q, nq, kp, S, seed, o, out, s, qbase);
 }
 
 cudaError_t launch_stoch_lane(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,

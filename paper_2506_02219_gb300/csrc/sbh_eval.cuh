@@ -8,14 +8,16 @@
 
 namespace sbh {
 
-// host_ctrl: the host copy of the tree's control block (node counts per generation)
+// host_ctrl: the host copy of the tree's control block (node counts per generation); qbase: the
+// index of Q[0] in the caller's whole query set, so that a chunk draws the random stream the whole
+// set would give it
 cudaError_t launch_stoch_eval(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
                               const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
-                              cudaStream_t s);
+                              cudaStream_t s, int64_t qbase = 0);
 
 cudaError_t launch_stoch_batched(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
                                  const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
-                                 cudaStream_t s);
+                                 cudaStream_t s, int64_t qbase = 0);
 
 // many sets in one launch: set_descs is a device array of n_sets descriptors filled with
 // multi_fill_desc (host side) and copied to the device; counter is one device word

@@ -172,6 +172,7 @@ struct Params {
     uint2 key;
     int sampling, rr, coherent, raw_sum;
     float* out;
+    int64_t qbase;           // index of the first query in the caller's whole query set (chunked runs)
     // learned proposal only
     const __half* mlpw;
     float near;
@@ -525,7 +526,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
     float3 q = make_float3(0.f, 0.f, 0.f);
     if (active) q = make_float3(P.Q[3 * j], P.Q[3 * j + 1], P.Q[3 * j + 2]);
     W.qx[lane] = q.x; W.qy[lane] = q.y; W.qz[lane] = q.z;
-    W.qctr[lane] = P.coherent ? 0u : (uint32_t)j;
+    W.qctr[lane] = P.coherent ? 0u : (uint32_t)(j + P.qbase);
     W.acc[lane] = 0.0f;
     W.ref[lane] = 3.0e38f;
     __syncwarp();
@@ -705,10 +706,11 @@ static cudaError_t launch_kind(const Params& P, unsigned blocks, int32_t lo, uin
 template <bool LEARNED>
 static cudaError_t launch_batched_impl(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
                                        const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o,
-                                       float* out, const void* mlp_half, float near, cudaStream_t s)
+                                       float* out, const void* mlp_half, float near, cudaStream_t s, int64_t qbase)
 {
     if (nq <= 0) return cudaSuccess;
     Params P;
+    P.qbase = qbase;
     P.T = T; P.Q = Q; P.nq = nq; P.kp = kp; P.S = S;
     P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     P.sampling = o.sampling; P.rr = o.rr; P.coherent = o.seed_mode; P.raw_sum = o.raw_sum; P.out = out;
@@ -740,16 +742,16 @@ static cudaError_t launch_batched_impl(const TreeView& T, const TreeCtrl& host_c
 
 cudaError_t launch_stoch_batched(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
                                  const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
-                                 cudaStream_t s)
+                                 cudaStream_t s, int64_t qbase)
 {
-    return launch_batched_impl<false>(T, host_ctrl, Q, nq, kp, S, seed, o, out, nullptr, 0.0f, s);
+    return launch_batched_impl<false>(T, host_ctrl, Q, nq, kp, S, seed, o, out, nullptr, 0.0f, s, qbase);
 }
 
 cudaError_t launch_stoch_batched_learned(const TreeView& T, const TreeCtrl& host_ctrl, const void* mlp_half,
                                          float near, const float* Q, int64_t nq, const KernelParams& kp, int S,
                                          uint64_t seed, const sbh_eval_opts& o, float* out, cudaStream_t s)
 {
-    return launch_batched_impl<true>(T, host_ctrl, Q, nq, kp, S, seed, o, out, mlp_half, near, s);
+    return launch_batched_impl<true>(T, host_ctrl, Q, nq, kp, S, seed, o, out, mlp_half, near, s, 0);
 }
 
 cudaError_t launch_stoch_multi(const void* set_descs, int n_sets, int64_t total_tiles, unsigned long long* counter,
@@ -762,7 +764,7 @@ cudaError_t launch_stoch_multi(const void* set_descs, int n_sets, int64_t total_
     M.total_tiles = total_tiles;
     M.counter = counter;
     Params& P = M.base;
-    P.T = TreeView{}; P.Q = nullptr; P.nq = 0; P.kp = kp; P.S = S; P.out = nullptr;
+    P.T = TreeView{}; P.Q = nullptr; P.nq = 0; P.kp = kp; P.S = S; P.out = nullptr; P.qbase = 0;
     P.mlpw = nullptr; P.near = 0.0f; P.frag = nullptr; P.learn = nullptr;
     P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     P.sampling = o.sampling; P.rr = o.rr; P.coherent = o.seed_mode; P.raw_sum = o.raw_sum;
