@@ -208,9 +208,9 @@ EVAL_SOURCES = ["paper_2506_02219_gb300/csrc/sbh_eval_batched.cu", "paper_2506_0
                 "paper_2506_02219_gb300/csrc/sbh_learned.cuh"]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per query of the estimator kernel from the committed ncu summary, if the kernel
-    sources still hash to what was profiled; else None."""
+def profiled_bytes(workload: str, key: str = "dram_bytes_per_query"):
+    """Bytes per query of the estimator kernel (DRAM, or L2 with key l2_bytes_per_query) from the
+    committed ncu summary, if the kernel sources still hash to what was profiled; else None."""
     path = os.path.join(ROOT, "profiles", f"k_stoch_batched_{workload}.md")
     if not os.path.exists(path):
         return None
@@ -220,9 +220,18 @@ def profiled_traffic(workload: str):
         if ln.startswith("<!-- ") and "=" in ln:
             k, v = ln[5:].strip().rstrip("->").strip().split("=", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("source_hash") != want or "dram_bytes_per_query" not in vals:
+    if vals.get("source_hash") != want or key not in vals:
         return None
-    return float(vals["dram_bytes_per_query"])
+    return float(vals[key])
+
+
+def measured_hbm_gbs():
+    """The measured HBM copy bandwidth (GB/s) of this machine's GPUs, or None."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return None
 
 
 # ------------------------------------------------------------------------------------------------
@@ -370,10 +379,21 @@ def run_ours(args):
         sm_mhz = 2070.0
         peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
         achieved = flops / (eval_ms / 1e3) / 1e12
-        traffic_pq = profiled_traffic(args.workload)
+        traffic_pq = profiled_bytes(args.workload)
+        l2_pq = profiled_bytes(args.workload, "l2_bytes_per_query")
+        hbm_peak = measured_hbm_gbs()
+        memory = {}
+        if traffic_pq is not None:
+            gbs = traffic_pq * nq / (eval_ms / 1e3) / 1e9
+            memory["dram"] = {"achieved_gbs": gbs, "peak_gbs": hbm_peak, "peak_basis": "measured (MEASURED_PEAKS.json)",
+                              "frac": gbs / hbm_peak if hbm_peak else None, "bytes_per_query": traffic_pq}
+        if l2_pq is not None:
+            memory["l2"] = {"achieved_gbs": l2_pq * nq / (eval_ms / 1e3) / 1e9, "bytes_per_query": l2_pq,
+                            "note": "L2 sectors of one ncu capture (all sources) per query; no measured L2 peak"}
         result["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                               "frac": achieved / peak,
                               "traffic": (traffic_pq * nq) if traffic_pq is not None else None,
+                              "memory": memory,
                               "kernel": "k_stoch_batched", "terms_per_query": c[0] / nq,
                               "records_per_query": c[1] / nq, "decisions_per_query": c[2] / nq,
                               "flops_per_term": FLOPS_PER_TERM[wl.kernel],
