@@ -32,10 +32,6 @@ namespace {
 #ifndef SBH_GRID_BLOCKS_PER_SM
 #define SBH_GRID_BLOCKS_PER_SM 96
 #endif
-// child records in flight per lane in a swap task (2 or 4)
-#ifndef SBH_SWAP_WAYS
-#define SBH_SWAP_WAYS 2
-#endif
 
 constexpr int kWarpsPerBlock = 8;
 constexpr int kRing = 64;  // ring capacity per warp; at most 63 tasks wait at any time
@@ -89,11 +85,6 @@ __device__ __forceinline__ float4 ld_dip(const TreeView& T, const Stage& S, int3
     const uint32_t i = (uint32_t)(v - S.lo);
     return i < S.n ? S.dip[i] : __ldg(&T.dip[v]);
 }
-__device__ __forceinline__ float ld_cdf(const TreeView& T, const Stage& S, int32_t v)
-{
-    const uint32_t i = (uint32_t)(v - S.lo);
-    return i < S.n ? S.cdf[i] : __ldg(&T.cdf[v]);
-}
 __device__ __forceinline__ uint32_t ld_meta(const TreeView& T, const Stage& S, int32_t v)
 {
     const uint32_t i = (uint32_t)(v - S.lo);
@@ -124,10 +115,12 @@ __device__ __forceinline__ int pick_child(const TreeView& T, const Stage& S, int
 {
     if (sampling == 0) {
         const float u = unit24(x);
+        const bool st = f >= S.lo && (uint32_t)(f + nc - S.lo) <= S.n;
+        const float* cdf = st ? S.cdf + (f - S.lo) : T.cdf + f;
         int lo = 0, hi = nc - 1;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
-            if (ld_cdf(T, S, f + mid) <= u) lo = mid + 1;
+            if (cdf[mid] <= u) lo = mid + 1;
             else hi = mid;
         }
         return lo;
@@ -442,43 +435,41 @@ __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, Warp
         const int32_t f = ld_fc(T, S, node);
         const int nc = (int)meta_nchild(m);
         const float4 pT = ld_pm(T, S, node);
+        // the children are read through one pointer: all staged (a subdomain's children) or all
+        // from global memory (a node whose children straddle the end of the stage reads them there)
+        const bool st = f >= S.lo && (uint32_t)(f + nc - S.lo) <= S.n;
+        const float4* cp = st ? S.pm + (f - S.lo) : T.pm + f;
         if constexpr (KIND == SBH_SMOOTHDIST) {
             const float a = P.kp.alpha;
             r = dist_fast(pT, q);
             v = -w * pT.w;
             for (int k = 0; k < nc; ++k) {
-                const float4 pc = ld_pm(T, S, f + k);
+                const float4 pc = cp[k];
                 const float d = dist_fast(pc, q);
                 if (d < r) { v *= __expf(-a * (r - d)); r = d; }
                 v = fmaf(w * pc.w, __expf(-a * (d - r)), v);
             }
         } else {
-#if SBH_SWAP_WAYS == 4
-            // four independent partial sums: four child records in flight per iteration
-            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
-            int k = 0;
-            for (; k + 3 < nc; k += 4) {
-                const float4 p0 = ld_pm(T, S, f + k), p1 = ld_pm(T, S, f + k + 1);
-                const float4 p2 = ld_pm(T, S, f + k + 2), p3 = ld_pm(T, S, f + k + 3);
-                s0 += node_value<KIND>(T, S, f + k, p0, q, P.kp);
-                s1 += node_value<KIND>(T, S, f + k + 1, p1, q, P.kp);
-                s2 += node_value<KIND>(T, S, f + k + 2, p2, q, P.kp);
-                s3 += node_value<KIND>(T, S, f + k + 3, p3, q, P.kp);
-            }
-            for (; k < nc; ++k) s0 += node_value<KIND>(T, S, f + k, ld_pm(T, S, f + k), q, P.kp);
-            v = w * (((s0 + s1) + (s2 + s3)) - node_value<KIND>(T, S, node, pT, q, P.kp));
-#else
             // two independent partial sums: two child records in flight per iteration
+            const float4* cd = KIND == SBH_WINDING ? (st ? S.dip + (f - S.lo) : T.dip + f) : cp;
             float s0 = 0.0f, s1 = 0.0f;
             int k = 0;
             for (; k + 1 < nc; k += 2) {
-                const float4 p0 = ld_pm(T, S, f + k), p1 = ld_pm(T, S, f + k + 1);
-                s0 += node_value<KIND>(T, S, f + k, p0, q, P.kp);
-                s1 += node_value<KIND>(T, S, f + k + 1, p1, q, P.kp);
+                const float4 p0 = cp[k], p1 = cp[k + 1];
+                if constexpr (KIND == SBH_WINDING) {
+                    const float4 d0 = cd[k], d1 = cd[k + 1];
+                    s0 += term_winding(p0, d0, q);
+                    s1 += term_winding(p1, d1, q);
+                } else {
+                    s0 += node_value<KIND>(T, S, f + k, p0, q, P.kp);
+                    s1 += node_value<KIND>(T, S, f + k + 1, p1, q, P.kp);
+                }
             }
-            if (k < nc) s0 += node_value<KIND>(T, S, f + k, ld_pm(T, S, f + k), q, P.kp);
+            if (k < nc) {
+                if constexpr (KIND == SBH_WINDING) s0 += term_winding(cp[k], cd[k], q);
+                else s0 += node_value<KIND>(T, S, f + k, cp[k], q, P.kp);
+            }
             v = w * ((s0 + s1) - node_value<KIND>(T, S, node, pT, q, P.kp));
-#endif
         }
     }
     // lane-ordered sum over the tasks of each query
