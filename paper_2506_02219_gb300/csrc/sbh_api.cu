@@ -344,7 +344,7 @@ sbh_status sbh_eval_grad(const sbh_tree* tree, const float* queries, int64_t nq,
     if (nq == 0) return SBH_OK;
     if (!device_ptr(queries) || !device_ptr(out) || !device_ptr(grad))
         return fail(SBH_EINVAL, "queries, out and grad must be device memory");
-    cudaError_t e = sbh::launch_stoch_grad(tree->t4.view(), queries, nq, kp, samples_per_subdomain, seed, o, out, grad,
+    cudaError_t e = sbh::launch_stoch_grad(tree->t4.view(), tree->host_ctrl4, queries, nq, kp, samples_per_subdomain, seed, o, out, grad,
                                            (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "sbh_eval_grad launch");
     return SBH_OK;

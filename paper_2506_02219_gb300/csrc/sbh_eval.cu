@@ -289,10 +289,12 @@ cudaError_t launch_stoch_count(const TreeView& T, const float* Q, int64_t nq, co
     return launch_lane_impl<kModeCount>(T, Q, nq, kp, S, seed, o, nullptr, nullptr, counts, s);
 }
 
-cudaError_t launch_stoch_grad(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
-                              uint64_t seed, const sbh_eval_opts& o, float* out, float* grad, cudaStream_t s)
+cudaError_t launch_stoch_grad(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
+                              const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
+                              float* grad, cudaStream_t s)
 {
-    return launch_lane_impl<kModeGrad>(T, Q, nq, kp, S, seed, o, out, grad, nullptr, s);
+    if (o.schedule == 1) return launch_lane_impl<kModeGrad>(T, Q, nq, kp, S, seed, o, out, grad, nullptr, s);
+    return launch_stoch_batched_grad(T, host_ctrl, Q, nq, kp, S, seed, o, out, grad, s);
 }
 
 }  // namespace sbh

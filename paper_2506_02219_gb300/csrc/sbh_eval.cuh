@@ -41,8 +41,13 @@ cudaError_t launch_stoch_batched_learned(const TreeView& T, const TreeCtrl& host
 cudaError_t launch_stoch_count(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
                                uint64_t seed, const sbh_eval_opts& o, unsigned long long* counts, cudaStream_t s);
 
-cudaError_t launch_stoch_grad(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, int S,
-                              uint64_t seed, const sbh_eval_opts& o, float* out, float* grad, cudaStream_t s);
+// the adjoint: schedule 0 = the warp-task kernel, 1 = one thread per query
+cudaError_t launch_stoch_grad(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
+                              const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
+                              float* grad, cudaStream_t s);
+cudaError_t launch_stoch_batched_grad(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
+                                      const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
+                                      float* grad, cudaStream_t s);
 
 cudaError_t launch_bh_eval(const TreeView& T, const float* Q, int64_t nq, const KernelParams& kp, float beta,
                            int warp_vote, float* out, cudaStream_t s);

@@ -166,6 +166,8 @@ struct Params {
     int sampling, rr, coherent, raw_sum;
     float* out;
     int64_t qbase;           // index of the first query in the caller's whole query set (chunked runs)
+    float* grad;             // adjoint only: d out / d q, [nq][3]
+    float* gsum;             // adjoint only: shared memory, per warp the 32 queries' swap gradients [32][3]
     // learned proposal only
     const __half* mlpw;
     float near;
@@ -407,9 +409,59 @@ __device__ __forceinline__ void decision_batch(const Params& P, const Stage& S, 
     decide<KIND, LEARNED>(P, S, W, sdiam, valid, node, tag, ai, prr, dT, wT, wa, d_tail, s_tail);
 }
 
-// Run up to 32 swap tasks: w * (sum_children m_c f(p_c, q) - m_T f(p_T, q)), added to the
-// query's sum in lane order.
+// m f(p, q) and its gradient in q (added to g), for the adjoint: the kernel ∇_q f applied to the
+// same terms (dp: the node's dipole sum, winding kernel only)
 template <int KIND>
+__device__ __forceinline__ float term_vg(float4 pm, float4 dp, float3 q, const KernelParams& kp, float g[3])
+{
+    const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
+    if constexpr (KIND == SBH_COULOMB) {
+        const float e = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, kp.eps2)));
+        const float ir = rsqrtf(e);
+        const float t = pm.w * ir;
+        const float c = t * ir * ir;  // m / e^(3/2)
+        g[0] = fmaf(c, dx, g[0]); g[1] = fmaf(c, dy, g[1]); g[2] = fmaf(c, dz, g[2]);
+        return t;
+    } else if constexpr (KIND == SBH_WINDING) {
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (!(r2 > 0.0f)) return 0.0f;
+        const float ir = rsqrtf(r2);
+        const float ir3 = ir * ir * ir;
+        const float dn = fmaf(dx, dp.x, fmaf(dy, dp.y, dz * dp.z));
+        const float c = 3.0f * kInv4Pi * dn * ir3 * ir * ir;  // 3 (d.N) / (4 pi r^5)
+        const float b = -kInv4Pi * ir3;                       // -1 / (4 pi r^3)
+        g[0] += fmaf(b, dp.x, c * dx); g[1] += fmaf(b, dp.y, c * dy); g[2] += fmaf(b, dp.z, c * dz);
+        return kInv4Pi * dn * ir3;
+    } else {
+        g[0] -= pm.w * kp.g[0]; g[1] -= pm.w * kp.g[1]; g[2] -= pm.w * kp.g[2];
+        return pm.w * (1.0f + fmaf(kp.g[0], dx, fmaf(kp.g[1], dy, kp.g[2] * dz)));
+    }
+}
+
+// smooth distance: add m exp(-alpha (d - ref)) and its gradient to (v, g) in the frame exp(-alpha ref),
+// lowering ref to d first when d is smaller (v and g scale together)
+__device__ __forceinline__ void smooth_vg(float4 pm, float3 q, float alpha, float wm, float& ref, float& v, float g[3])
+{
+    const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ir = rsqrtf(fmaxf(r2, 1e-37f));
+    const float d = r2 * ir;
+    if (d < ref) {
+        const float f = __expf(-alpha * (ref - d));
+        v *= f; g[0] *= f; g[1] *= f; g[2] *= f;
+        ref = d;
+    }
+    const float t = wm * __expf(-alpha * (d - ref));
+    v += t;
+    if (r2 > 0.0f) {
+        const float c = alpha * t * ir;  // alpha m exp(-alpha d) / d
+        g[0] = fmaf(c, dx, g[0]); g[1] = fmaf(c, dy, g[1]); g[2] = fmaf(c, dz, g[2]);
+    }
+}
+
+// Run up to 32 swap tasks: w * (sum_children m_c f(p_c, q) - m_T f(p_T, q)), added to the
+// query's sum in lane order. GRAD: the same for the terms' query gradients.
+template <int KIND, bool GRAD>
 __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, WarpState& W, uint32_t& s_head,
                                            uint32_t s_tail)
 {
@@ -429,6 +481,7 @@ __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, Warp
     __syncwarp();
     s_head += take;
     float v = 0.0f, r = 3.0e38f;
+    float g[3] = {0.0f, 0.0f, 0.0f};
     if (valid) {
         const float3 q = make_float3(W.qx[slot], W.qy[slot], W.qz[slot]);
         const uint32_t m = ld_meta(T, S, node);
@@ -439,7 +492,20 @@ __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, Warp
         // from global memory (a node whose children straddle the end of the stage reads them there)
         const bool st = f >= S.lo && (uint32_t)(f + nc - S.lo) <= S.n;
         const float4* cp = st ? S.pm + (f - S.lo) : T.pm + f;
-        if constexpr (KIND == SBH_SMOOTHDIST) {
+        if constexpr (GRAD && KIND == SBH_SMOOTHDIST) {
+            const float a = P.kp.alpha;
+            smooth_vg(pT, q, a, -w * pT.w, r, v, g);
+            for (int k = 0; k < nc; ++k) smooth_vg(cp[k], q, a, w * cp[k].w, r, v, g);
+        } else if constexpr (GRAD) {
+            const float4* cd = KIND == SBH_WINDING ? (st ? S.dip + (f - S.lo) : T.dip + f) : cp;
+            float s0 = 0.0f;
+            for (int k = 0; k < nc; ++k) s0 += term_vg<KIND>(cp[k], cd[k], q, P.kp, g);
+            float go[3] = {0.0f, 0.0f, 0.0f};
+            const float4 dT = KIND == SBH_WINDING ? ld_dip(T, S, node) : pT;
+            const float own = term_vg<KIND>(pT, dT, q, P.kp, go);
+            v = w * (s0 - own);
+            g[0] = w * (g[0] - go[0]); g[1] = w * (g[1] - go[1]); g[2] = w * (g[2] - go[2]);
+        } else if constexpr (KIND == SBH_SMOOTHDIST) {
             const float a = P.kp.alpha;
             r = dist_fast(pT, q);
             v = -w * pT.w;
@@ -475,28 +541,53 @@ __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, Warp
     // lane-ordered sum over the tasks of each query
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, slot);
     float tot = 0.0f, tr = 3.0e38f;
+    float tg[3] = {0.0f, 0.0f, 0.0f};
     for (unsigned rest = peers; rest; rest &= rest - 1u) {
         const int src = __ffs(rest) - 1;
         const float vs = __shfl_sync(peers, v, src);
+        float gs[3] = {0.0f, 0.0f, 0.0f};
+        if constexpr (GRAD) {
+            gs[0] = __shfl_sync(peers, g[0], src); gs[1] = __shfl_sync(peers, g[1], src);
+            gs[2] = __shfl_sync(peers, g[2], src);
+        }
         if constexpr (KIND == SBH_SMOOTHDIST) {
             const float rs = __shfl_sync(peers, r, src);
             const float a = P.kp.alpha;
-            if (rs < tr) { tot = tot * __expf(-a * (tr - rs)) + vs; tr = rs; }
-            else tot = fmaf(vs, __expf(-a * (rs - tr)), tot);
+            if (rs < tr) {
+                const float f = __expf(-a * (tr - rs));
+                tot = tot * f + vs;
+                if (GRAD) for (int c = 0; c < 3; ++c) tg[c] = tg[c] * f + gs[c];
+                tr = rs;
+            } else {
+                const float f = __expf(-a * (rs - tr));
+                tot = fmaf(vs, f, tot);
+                if (GRAD) for (int c = 0; c < 3; ++c) tg[c] = fmaf(gs[c], f, tg[c]);
+            }
         } else {
             tot += vs;
+            if (GRAD) for (int c = 0; c < 3; ++c) tg[c] += gs[c];
         }
     }
     if (valid && lane_id() == (uint32_t)(__ffs(peers) - 1)) {
+        float* qg = GRAD ? P.gsum + (threadIdx.x >> 5) * 96 + 3 * slot : nullptr;
         if constexpr (KIND == SBH_SMOOTHDIST) {
             const float a = P.kp.alpha;
             float qr = W.ref[slot], qa = W.acc[slot];
-            if (tr < qr) { qa = qa * __expf(-a * (qr - tr)) + tot; qr = tr; }
-            else qa = fmaf(tot, __expf(-a * (tr - qr)), qa);
+            if (tr < qr) {
+                const float f = __expf(-a * (qr - tr));
+                qa = qa * f + tot;
+                if (GRAD) for (int c = 0; c < 3; ++c) qg[c] = qg[c] * f + tg[c];
+                qr = tr;
+            } else {
+                const float f = __expf(-a * (tr - qr));
+                qa = fmaf(tot, f, qa);
+                if (GRAD) for (int c = 0; c < 3; ++c) qg[c] = fmaf(tg[c], f, qg[c]);
+            }
             W.ref[slot] = qr;
             W.acc[slot] = qa;
         } else {
             W.acc[slot] += tot;
+            if (GRAD) for (int c = 0; c < 3; ++c) qg[c] += tg[c];
         }
     }
     __syncwarp();
@@ -504,7 +595,7 @@ __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, Warp
 
 // One tile of 32 queries (query index tile * 32 + lane within the set described by P), run by
 // one warp: control variates and depth-0 decisions lane-parallel, everything else as tasks.
-template <int KIND, bool LEARNED>
+template <int KIND, bool LEARNED, bool GRAD>
 __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpState& W, const float* sdiam,
                                          int64_t tile)
 {
@@ -520,8 +611,11 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
     W.qctr[lane] = P.coherent ? 0u : (uint32_t)(j + P.qbase);
     W.acc[lane] = 0.0f;
     W.ref[lane] = 3.0e38f;
+    float* qg = GRAD ? P.gsum + (threadIdx.x >> 5) * 96 + 3 * lane : nullptr;
+    if (GRAD) { qg[0] = 0.0f; qg[1] = 0.0f; qg[2] = 0.0f; }
     __syncwarp();
     float cv = 0.0f;
+    float cg[3] = {0.0f, 0.0f, 0.0f};  // GRAD: the control variates' gradient (in the frame of ex)
     ExpAcc ex;
     ex.init(3.0e38f);
     uint32_t d_head = 0, d_tail = 0, s_head = 0, s_tail = 0;
@@ -531,7 +625,11 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
         const float4 pa = ld_pm(T, S, a);
         const uint32_t ma = ld_meta(T, S, a);
         if (active) {  // control variate CV_a
-            if constexpr (KIND == SBH_SMOOTHDIST) {
+            if constexpr (GRAD && KIND == SBH_SMOOTHDIST) {
+                smooth_vg(pa, q, P.kp.alpha, pa.w, ex.ref, ex.acc, cg);
+            } else if constexpr (GRAD) {
+                cv += term_vg<KIND>(pa, KIND == SBH_WINDING ? ld_dip(T, S, a) : pa, q, P.kp, cg);
+            } else if constexpr (KIND == SBH_SMOOTHDIST) {
                 const float d = dist_fast(pa, q);
                 ex.lower(d, P.kp.alpha);
                 ex.acc = fmaf(pa.w, ex.scale(d, P.kp.alpha), ex.acc);
@@ -545,16 +643,16 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
         for (int s = 0; s < P.S; ++s) {
             decide<KIND, LEARNED>(P, S, W, sdiam, active, a, lane | ((uint32_t)s << 13), ai, 1.0f, da, wa, wa, d_tail,
                                   s_tail);
-            while (s_tail - s_head >= 32u) swap_batch<KIND>(P, S, W, s_head, s_tail);
+            while (s_tail - s_head >= 32u) swap_batch<KIND, GRAD>(P, S, W, s_head, s_tail);
             while (d_tail - d_head >= 32u) {
                 decision_batch<KIND, LEARNED>(P, S, W, sdiam, d_head, d_tail, s_tail);
-                while (s_tail - s_head >= 32u) swap_batch<KIND>(P, S, W, s_head, s_tail);
+                while (s_tail - s_head >= 32u) swap_batch<KIND, GRAD>(P, S, W, s_head, s_tail);
             }
         }
     }
     // drain the partial batches
     while (d_tail != d_head || s_tail != s_head) {
-        if (s_tail != s_head) swap_batch<KIND>(P, S, W, s_head, s_tail);
+        if (s_tail != s_head) swap_batch<KIND, GRAD>(P, S, W, s_head, s_tail);
         if (d_tail != d_head) decision_batch<KIND, LEARNED>(P, S, W, sdiam, d_head, d_tail, s_tail);
     }
     __syncwarp();
@@ -562,26 +660,49 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
         if constexpr (KIND == SBH_SMOOTHDIST) {
             const float a = P.kp.alpha;
             float r = W.ref[lane], v = W.acc[lane];
+            float sg[3] = {0.0f, 0.0f, 0.0f};
+            if (GRAD) { sg[0] = qg[0]; sg[1] = qg[1]; sg[2] = qg[2]; }
             // merge the swap sum into the control-variate sum
-            if (r < ex.ref) { ex.acc = ex.acc * __expf(-a * (ex.ref - r)) + v; ex.ref = r; }
-            else ex.acc = fmaf(v, __expf(-a * (r - ex.ref)), ex.acc);
-            if (P.raw_sum) P.out[j] = ex.acc * __expf(-a * ex.ref);
-            else P.out[j] = ex.acc > 0.0f ? ex.ref - __logf(ex.acc) / a : __int_as_float(0x7F800000);
+            if (r < ex.ref) {
+                const float f = __expf(-a * (ex.ref - r));
+                ex.acc = ex.acc * f + v;
+                if (GRAD) for (int c = 0; c < 3; ++c) cg[c] = cg[c] * f + sg[c];
+                ex.ref = r;
+            } else {
+                const float f = __expf(-a * (r - ex.ref));
+                ex.acc = fmaf(v, f, ex.acc);
+                if (GRAD) for (int c = 0; c < 3; ++c) cg[c] = fmaf(sg[c], f, cg[c]);
+            }
+            if (P.raw_sum) {
+                const float sc = __expf(-a * ex.ref);
+                P.out[j] = ex.acc * sc;
+                if (GRAD) for (int c = 0; c < 3; ++c) P.grad[3 * j + c] = cg[c] * sc;
+            } else {
+                const bool pos = ex.acc > 0.0f;
+                P.out[j] = pos ? ex.ref - __logf(ex.acc) / a : __int_as_float(0x7F800000);
+                if (GRAD) {  // d = ref - log(acc) / alpha: grad d = -grad acc / (alpha acc), the frame cancels
+                    const float c0 = pos ? -1.0f / (a * ex.acc) : __int_as_float(0x7FC00000);
+                    for (int c = 0; c < 3; ++c) P.grad[3 * j + c] = c0 * cg[c];
+                }
+            }
         } else {
             P.out[j] = cv + W.acc[lane];
+            if (GRAD) for (int c = 0; c < 3; ++c) P.grad[3 * j + c] = cg[c] + qg[c];
         }
     }
     __syncwarp();
 }
 
-// dynamic shared memory: [learned proposal: MlpFrag, one LearnScratch per warp] then the stage
-template <bool LEARNED>
-constexpr size_t learned_smem_bytes()
+// dynamic shared memory: [learned proposal: MlpFrag, one LearnScratch per warp | adjoint: one
+// [32][3] gradient sum per warp] then the stage
+template <bool LEARNED, bool GRAD>
+constexpr size_t extra_smem_bytes()
 {
-    return LEARNED ? sizeof(MlpFrag) + kWarpsPerBlock * sizeof(LearnScratch) : 0;
+    return LEARNED ? sizeof(MlpFrag) + kWarpsPerBlock * sizeof(LearnScratch)
+                   : (GRAD ? kWarpsPerBlock * 96 * sizeof(float) : 0);
 }
 
-template <int KIND, bool LEARNED>
+template <int KIND, bool LEARNED, bool GRAD>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, LEARNED ? 2 : SBH_BATCHED_MIN_BLOCKS)
     k_stoch_batched(Params P, int32_t stage_lo, uint32_t stage_n)
 {
@@ -594,7 +715,10 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, LEARNED ? 2 : SBH_BATCHED
         mlp_frag_fill(P.mlpw, *F);
         P.frag = F;
         P.learn = reinterpret_cast<LearnScratch*>(reinterpret_cast<unsigned char*>(s_dyn) + sizeof(MlpFrag));
-        s_stage = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_dyn) + learned_smem_bytes<LEARNED>());
+        s_stage = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_dyn) + extra_smem_bytes<LEARNED, GRAD>());
+    } else if constexpr (GRAD) {
+        P.gsum = reinterpret_cast<float*>(s_dyn);
+        s_stage = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_dyn) + extra_smem_bytes<LEARNED, GRAD>());
     }
     Stage S;
     S.lo = stage_lo;
@@ -621,7 +745,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, LEARNED ? 2 : SBH_BATCHED
     const int64_t n_tiles = (P.nq + 31) / 32;
     const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t warp_stride = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t tile = warp_global; tile < n_tiles; tile += warp_stride) run_tile<KIND, LEARNED>(P, S, W, sdiam, tile);
+    for (int64_t tile = warp_global; tile < n_tiles; tile += warp_stride)
+        run_tile<KIND, LEARNED, GRAD>(P, S, W, sdiam, tile);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -678,30 +803,33 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_stoch_multi(MultiPar
             if (lane < (uint32_t)kDiamLevels) sdiam[lane] = D.T.ctrl->diam[lane];
             __syncwarp();
         }
-        run_tile<KIND, false>(P, S, W, sdiam, tile - M.sets[lo].tile_begin);
+        run_tile<KIND, false, false>(P, S, W, sdiam, tile - M.sets[lo].tile_begin);
     }
 }
 
-template <int KIND, bool LEARNED>
+template <int KIND, bool LEARNED, bool GRAD>
 static cudaError_t launch_kind(const Params& P, unsigned blocks, int32_t lo, uint32_t n, cudaStream_t s)
 {
-    const size_t bytes = learned_smem_bytes<LEARNED>() +
+    const size_t bytes = extra_smem_bytes<LEARNED, GRAD>() +
                          (size_t)n * (sizeof(float4) * (KIND == SBH_WINDING ? 2 : 1) + 3 * sizeof(uint32_t));
-    cudaError_t e = cudaFuncSetAttribute(k_stoch_batched<KIND, LEARNED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_stoch_batched<KIND, LEARNED, GRAD>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_stoch_batched<KIND, LEARNED><<<blocks, 32 * kWarpsPerBlock, bytes, s>>>(P, lo, n);
+    k_stoch_batched<KIND, LEARNED, GRAD><<<blocks, 32 * kWarpsPerBlock, bytes, s>>>(P, lo, n);
     return cudaSuccess;
 }
 
-template <bool LEARNED>
+template <bool LEARNED, bool GRAD = false>
 static cudaError_t launch_batched_impl(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
                                        const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o,
-                                       float* out, const void* mlp_half, float near, cudaStream_t s, int64_t qbase)
+                                       float* out, const void* mlp_half, float near, cudaStream_t s, int64_t qbase,
+                                       float* grad = nullptr)
 {
     if (nq <= 0) return cudaSuccess;
     Params P;
     P.qbase = qbase;
+    P.grad = grad;
+    P.gsum = nullptr;
     P.T = T; P.Q = Q; P.nq = nq; P.kp = kp; P.S = S;
     P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     P.sampling = o.sampling; P.rr = o.rr; P.coherent = o.seed_mode; P.raw_sum = o.raw_sum; P.out = out;
@@ -718,10 +846,10 @@ static cudaError_t launch_batched_impl(const TreeView& T, const TreeCtrl& host_c
     if (n > cap) n = cap;
     cudaError_t e;
     switch (kp.kind) {
-    case SBH_COULOMB: e = launch_kind<SBH_COULOMB, LEARNED>(P, (unsigned)blocks, lo, n, s); break;
-    case SBH_WINDING: e = launch_kind<SBH_WINDING, LEARNED>(P, (unsigned)blocks, lo, n, s); break;
-    case SBH_SMOOTHDIST: e = launch_kind<SBH_SMOOTHDIST, LEARNED>(P, (unsigned)blocks, lo, n, s); break;
-    case SBH_AFFINE: e = launch_kind<SBH_AFFINE, LEARNED>(P, (unsigned)blocks, lo, n, s); break;
+    case SBH_COULOMB: e = launch_kind<SBH_COULOMB, LEARNED, GRAD>(P, (unsigned)blocks, lo, n, s); break;
+    case SBH_WINDING: e = launch_kind<SBH_WINDING, LEARNED, GRAD>(P, (unsigned)blocks, lo, n, s); break;
+    case SBH_SMOOTHDIST: e = launch_kind<SBH_SMOOTHDIST, LEARNED, GRAD>(P, (unsigned)blocks, lo, n, s); break;
+    case SBH_AFFINE: e = launch_kind<SBH_AFFINE, LEARNED, GRAD>(P, (unsigned)blocks, lo, n, s); break;
     default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
@@ -736,6 +864,13 @@ cudaError_t launch_stoch_batched(const TreeView& T, const TreeCtrl& host_ctrl, c
                                  cudaStream_t s, int64_t qbase)
 {
     return launch_batched_impl<false>(T, host_ctrl, Q, nq, kp, S, seed, o, out, nullptr, 0.0f, s, qbase);
+}
+
+cudaError_t launch_stoch_batched_grad(const TreeView& T, const TreeCtrl& host_ctrl, const float* Q, int64_t nq,
+                                      const KernelParams& kp, int S, uint64_t seed, const sbh_eval_opts& o, float* out,
+                                      float* grad, cudaStream_t s)
+{
+    return launch_batched_impl<false, true>(T, host_ctrl, Q, nq, kp, S, seed, o, out, nullptr, 0.0f, s, 0, grad);
 }
 
 cudaError_t launch_stoch_batched_learned(const TreeView& T, const TreeCtrl& host_ctrl, const void* mlp_half,
@@ -756,6 +891,7 @@ cudaError_t launch_stoch_multi(const void* set_descs, int n_sets, int64_t total_
     M.counter = counter;
     Params& P = M.base;
     P.T = TreeView{}; P.Q = nullptr; P.nq = 0; P.kp = kp; P.S = S; P.out = nullptr; P.qbase = 0;
+    P.grad = nullptr; P.gsum = nullptr;
     P.mlpw = nullptr; P.near = 0.0f; P.frag = nullptr; P.learn = nullptr;
     P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     P.sampling = o.sampling; P.rr = o.rr; P.coherent = o.seed_mode; P.raw_sum = o.raw_sum;

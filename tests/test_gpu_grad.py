@@ -1,7 +1,8 @@
 """The adjoint (sbh_eval_grad) on the GPU against the oracle.
 
 - Parity with the oracle's gradient replay (same paths and weights, FP32 decisions on both
-  sides): |g_gpu - g_oracle| <= 1e-4 * A_g on >= 99.9% of queries, A_g the sum of |gradient terms|.
+  sides): |g_gpu - g_oracle| <= 1e-4 * A_g on >= 99.9% of queries, A_g the sum of |gradient terms|,
+  for the warp-task kernel and the one-thread-per-query kernel.
 - Unbiasedness: averaged over seeds, the GPU gradient of the sum lies within 3 sigma of the
   FP64 brute-force gradient of Eq. 1.
 - Finite differences: with the roulette off (p = 1) and mass-proportional picks no decision and no
@@ -39,13 +40,14 @@ def _inputs(kind, n, nq, seed):
 
 
 @pytest.mark.parametrize("kind", ["coulomb", "winding", "smoothdist", "affine"])
-@pytest.mark.parametrize("S", [1, 2])
-def test_adjoint_matches_oracle(sbh, oracle_mod, kind, S):
+@pytest.mark.parametrize("S,schedule", [(1, 0), (2, 0), (1, 1), (2, 1)])
+def test_adjoint_matches_oracle(sbh, oracle_mod, kind, S, schedule):
     pts, w, nrm, q = _inputs(kind, 10000, 2001, 61 + S)
     alpha = 30.0
     t = sbh.sbh_build(dev(pts), dev(w), dev(nrm))
     o = sbh.EvalOpts()
     o.raw_sum = 1  # smooth distance: compare the sum and its gradient
+    o.schedule = schedule  # 0: warp-task kernel, 1: one thread per query
     val, g = sbh.sbh_eval_grad(t, dev(q), samples_per_subdomain=S, seed=5, opts=o, **gpu_kwargs(kind, alpha=alpha))
     val, g = val.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64)
     ot = oracle_mod.Tree(pts, w, nrm, leaf_size=1, d=4)
@@ -76,12 +78,14 @@ def test_adjoint_is_unbiased(sbh, oracle_mod, kind):
 
 
 @pytest.mark.parametrize("kind", ["coulomb", "winding", "smoothdist"])
-def test_adjoint_matches_finite_differences_without_roulette(sbh, oracle_mod, kind):
+@pytest.mark.parametrize("schedule", [0, 1])
+def test_adjoint_matches_finite_differences_without_roulette(sbh, oracle_mod, kind, schedule):
     pts, w, nrm, q = _inputs(kind, 20000, 81, 512)
     t = sbh.sbh_build(dev(pts), dev(w), dev(nrm))
     kw = gpu_kwargs(kind, alpha=200.0)
     o = sbh.EvalOpts()
     o.rr = 1
+    o.schedule = schedule
     d0, g = sbh.sbh_eval_grad(t, dev(q), seed=9, opts=o, **kw)
     d0, g = d0.cpu().numpy().astype(np.float64), g.cpu().numpy().astype(np.float64)
     ok = np.isfinite(d0)
