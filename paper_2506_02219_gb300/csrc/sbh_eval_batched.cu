@@ -22,11 +22,12 @@ namespace sbh {
 namespace {
 
 // resident blocks per SM the register budget is set for, and the most nodes staged per block
+// (4 and 128 measured best: more warps in flight beat a deeper stage, which L1 mostly covers)
 #ifndef SBH_BATCHED_MIN_BLOCKS
-#define SBH_BATCHED_MIN_BLOCKS 3
+#define SBH_BATCHED_MIN_BLOCKS 4
 #endif
 #ifndef SBH_STAGE_MAX
-#define SBH_STAGE_MAX 2048
+#define SBH_STAGE_MAX 128
 #endif
 // most blocks launched per SM (the rest of the tiles are taken in grid-stride order)
 #ifndef SBH_GRID_BLOCKS_PER_SM
@@ -772,7 +773,7 @@ struct MultiParams {
 };
 
 template <int KIND>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 3) k_stoch_multi(MultiParams M)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, SBH_BATCHED_MIN_BLOCKS) k_stoch_multi(MultiParams M)
 {
     __shared__ WarpState s_state[kWarpsPerBlock];
     __shared__ float s_diam[kWarpsPerBlock][kDiamLevels];
@@ -897,8 +898,8 @@ cudaError_t launch_stoch_multi(const void* set_descs, int n_sets, int64_t total_
     P.sampling = o.sampling; P.rr = o.rr; P.coherent = o.seed_mode; P.raw_sum = o.raw_sum;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    // persistent: three blocks per SM
-    const unsigned blocks = 152 * 3;
+    // persistent: as many blocks as are resident at once
+    const unsigned blocks = 152 * SBH_BATCHED_MIN_BLOCKS;
     switch (kp.kind) {
     case SBH_COULOMB: k_stoch_multi<SBH_COULOMB><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(M); break;
     case SBH_WINDING: k_stoch_multi<SBH_WINDING><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(M); break;
