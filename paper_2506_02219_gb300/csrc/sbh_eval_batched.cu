@@ -62,8 +62,9 @@ struct WarpState {
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << lane_id()) - 1u; }
 
-// The subdomains and their children (node generations 1 and 2) are read by every query: each
-// block copies them (up to kStageMax nodes) into shared memory at start and reads them there.
+// The subdomains (node generation 1) are read by every query: each block copies the first
+// kStageMax nodes of generations 1 and 2 (the subdomains, then the first of their children) into
+// shared memory at start and reads them there; everything else is read through L1.
 constexpr int kStageMax = SBH_STAGE_MAX;
 
 struct Stage {
@@ -838,8 +839,8 @@ static cudaError_t launch_batched_impl(const TreeView& T, const TreeCtrl& host_c
     const int64_t tiles = (nq + 31) / 32;
     int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks > 152 * SBH_GRID_BLOCKS_PER_SM) blocks = 152 * SBH_GRID_BLOCKS_PER_SM;
-    // stage generations 1 and 2 (the subdomains and their children), at most kStageMax nodes
-    // (half as many with the learned proposal, whose scratch takes the rest of the room)
+    // stage the first nodes of generations 1 and 2 (the subdomains, then their children), at most
+    // kStageMax (half as many with the learned proposal, whose scratch takes room)
     const int32_t lo = host_ctrl.max_depth >= 1 ? host_ctrl.depth_base[1] : 0;
     const int32_t hi = host_ctrl.depth_base[host_ctrl.max_depth >= 2 ? 3 : (host_ctrl.max_depth >= 1 ? 2 : 1)];
     uint32_t n = (uint32_t)(hi > lo ? hi - lo : 0);
