@@ -60,6 +60,8 @@ def workload_by_name(name: str, rank: int = 0):
         return W.slice_plane_shapes(kernel="coulomb", seed=b + 2 + 1000 * rank)
     if name == "slice_smoothdist":
         return W.slice_plane_shapes(kernel="smoothdist", seed=b + 2 + 1000 * rank)
+    if name == "far_coulomb":
+        return W.far_field_coulomb(seed=b + 1 + 1000 * rank)
     raise ValueError(name)
 
 
@@ -695,7 +697,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="winding",
-                    choices=["winding", "cube", "slice_coulomb", "slice_smoothdist", "batched"])
+                    choices=["winding", "cube", "slice_coulomb", "slice_smoothdist", "far_coulomb", "batched"])
     ap.add_argument("--S", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-equal-error", action="store_true")

@@ -246,6 +246,18 @@ def slice_plane_shapes(n_sources: int = 1 << 22, res: int = 1000, kernel: str = 
     return Workload(f"{kernel}_shapes_{n_sources}src_{res}x{res}plane", p, w, nv, q, kernel, alpha=200.0)
 
 
+def far_field_coulomb(n_sources: int = 1 << 20, res: int = 170, seed: int = BASE_SEED + 1) -> Workload:
+    """The geometry of winding_ellipsoids (2^20 area-weighted samples, rescaled into [-1, 1]^3) with
+    the Coulomb kernel, queried in empty space around it: the nodes of a res^3 grid over [-3, 3]^3
+    that lie outside [-1.2, 1.2]^3 (the regime where most sources are far from every query)."""
+    p, w, nv = shape_union(n_sources, seed, n_ellipsoids=8, n_boxes=0)
+    g = np.linspace(-3.0, 3.0, res, dtype=np.float32)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    q = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+    q = np.ascontiguousarray(q[np.abs(q).max(1) > 1.2], dtype=np.float32)
+    return Workload(f"far_field_coulomb_{n_sources}src_{q.shape[0]}q", p, w, nv, q, "coulomb")
+
+
 def sphere_fibonacci(n: int, radius: float = 1.0):
     """n Fibonacci-lattice points on a sphere with equal area weights and outward normals."""
     i = np.arange(n, dtype=np.float64) + 0.5
