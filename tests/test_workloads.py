@@ -36,3 +36,10 @@ def test_heavier_sources_option():
     ratio = w1 / w0
     heavy = np.isclose(ratio, 5.0, rtol=1e-6)
     assert heavy.sum() == 400 and np.allclose(ratio[~heavy], 1.0)
+
+
+def test_far_field_queries_lie_outside_the_sources():
+    wl = W.far_field_coulomb(n_sources=5000, res=40)
+    assert wl.kernel == "coulomb" and wl.points.shape == (5000, 3)
+    assert np.all(np.abs(wl.queries).max(1) > 1.2) and np.all(np.abs(wl.queries) <= 3.0)
+    assert np.all(np.abs(wl.points) <= 1.0)
