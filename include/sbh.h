@@ -194,6 +194,7 @@ SBH_API sbh_status sbh_multi_plan_create(const sbh_tree* const* trees, const flo
                                          int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
                                          void* stream, sbh_multi_plan** plan);
 SBH_API sbh_status sbh_multi_plan_launch(const sbh_multi_plan* plan, void* stream);
+/* Release a plan's device memory (NULL is a no-op); synchronises the device first. */
 SBH_API void sbh_multi_plan_free(sbh_multi_plan* plan);
 
 /* Learned child proposal (the paper samples the path index uniformly and leaves importance
@@ -253,6 +254,7 @@ SBH_API sbh_status sbh_mlp_train(sbh_mlp* net, const sbh_tree* tree, const float
 SBH_API sbh_status sbh_eval_learned(const sbh_tree* tree, const sbh_mlp* net, const float* queries, int64_t nq,
                                     sbh_kernel kernel, int32_t samples_per_subdomain, uint64_t seed,
                                     const sbh_eval_opts* opts, float near, float* out, void* stream);
+/* Release a network's device memory (NULL is a no-op); synchronises the device first. */
 SBH_API void sbh_mlp_free(sbh_mlp* net);
 
 /* Device memory. Every buffer the library holds (trees, scratch, plans, networks) comes from a
