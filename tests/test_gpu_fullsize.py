@@ -2,8 +2,9 @@
 evaluates every query; a seeded sample of outputs is checked against the oracle, which replays
 those queries with their indices in the full set (the random stream is keyed by query index).
 
-Workloads: winding numbers of 2^20 oriented samples on 8 ellipsoids at 256^3 grid queries;
-Coulomb and smooth distance of 2^22 samples on ellipsoids and boxes at a shuffled 1000^2 plane.
+Workloads: winding numbers of 2^20 oriented samples on 8 ellipsoids at 256^3 grid queries (the
+estimate and its adjoint); Coulomb and smooth distance of 2^22 samples on ellipsoids and boxes at a
+shuffled 1000^2 plane.
 """
 import numpy as np
 import pytest
@@ -74,3 +75,19 @@ def test_seed_mean_full_size(sbh, oracle_mod, slice_wl):
     se = est.std(0, ddof=1) / np.sqrt(48)
     z = np.abs(est.mean(0) - F) / np.maximum(se, 1e-12 * F)
     assert np.mean(z <= 3.0) >= 0.97, np.sort(z)[-10:]
+
+
+def test_adjoint_full_size(sbh, oracle_mod, winding_wl):
+    """The adjoint (warp-task kernel, the bench's launch) on the whole winding workload: a sample of
+    its gradients against the oracle's gradient replay of the same queries with their indices."""
+    wl = winding_wl
+    t = sbh.sbh_build(dev(wl.points), dev(wl.weights), dev(wl.normals))
+    _, g = sbh.sbh_eval_grad(t, dev(wl.queries), seed=0x5BA7, **gpu_kwargs("winding"))
+    g = g.cpu().numpy().astype(np.float64)
+    idx = np.sort(np.random.default_rng(3).choice(wl.queries.shape[0], N_SAMPLE, replace=False))
+    ot = oracle_mod.Tree(wl.points, wl.weights, wl.normals, leaf_size=1, d=4)
+    _, og, A = ot.replay_grad(wl.queries[idx], S=1, seed=0x5BA7, query_index=idx,
+                              **oracle_kwargs(oracle_mod, "winding"))
+    err = np.abs(g[idx] - og).max(1) / np.maximum(A, 1.0)
+    assert np.mean(err <= 1e-4) >= 0.999, np.sort(err)[-5:]
+    assert np.all(np.isfinite(g))
