@@ -252,7 +252,12 @@ sbh_status sbh_solve_host(const float* points, const float* weights, const float
     if (e == cudaSuccess && normals) e = sbh::dalloc((void**)&dN, (size_t)n * 3 * sizeof(float), s);
     if (e == cudaSuccess && nq > 0) e = sbh::dalloc((void**)&dQ, (size_t)nq * 3 * sizeof(float), s);
     if (e == cudaSuccess && nq > 0) e = sbh::dalloc((void**)&dO, (size_t)nq * sizeof(float), s);
-    // the queries go in chunk by chunk on the copy stream, overlapping the build
+    // the sources go first (the build needs them; uploads share the copy engine), then the
+    // queries chunk by chunk on the copy stream, overlapping the build
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dP, points, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dW, weights, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && normals)
+        e = cudaMemcpyAsync(dN, normals, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(ci, ev[0], 0);
     for (int64_t k = 0; k < n_chunks && e == cudaSuccess; ++k) {
@@ -260,10 +265,6 @@ sbh_status sbh_solve_host(const float* points, const float* weights, const float
         e = cudaMemcpyAsync(dQ + 3 * b, queries + 3 * b, (size_t)m * 3 * sizeof(float), cudaMemcpyHostToDevice, ci);
         if (e == cudaSuccess) e = cudaEventRecord(ev[(size_t)(1 + k)], ci);
     }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dP, points, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dW, weights, (size_t)n * sizeof(float), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && normals)
-        e = cudaMemcpyAsync(dN, normals, (size_t)n * 3 * sizeof(float), cudaMemcpyHostToDevice, s);
     sbh_tree* tree = nullptr;
     if (e == cudaSuccess) {
         st = sbh_build(dP, dW, dN, n, leaf_size, (void*)s, &tree);  // synchronises s
