@@ -11,6 +11,11 @@
 // wait in two per-warp rings in shared memory and are run 32 at a time, one per lane, so the
 // lanes stay busy however the paths of the 32 queries diverge. Swap results reach a query's sum
 // through a lane-ordered reduction among the tasks of that query, so results are deterministic.
+//
+// Three instances share this schedule: the estimator; its adjoint (GRAD: every term also adds its
+// query gradient, with the same weights); and the learned child proposal (LEARNED: the children of
+// a batch's gated decisions are scored together on the tensor cores, see learned_picks). One more
+// kernel, k_stoch_multi, runs many independent problems in one persistent launch.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
