@@ -187,6 +187,13 @@ def interp_loglog(x_target, xs, ys):
     return float(np.exp(np.interp(t, lx, ly))), False
 
 
+def tail_errors(rel):
+    """Mean and 99th percentile of per-query relative errors (finite ones)."""
+    r = np.asarray(rel, np.float64)
+    r = r[np.isfinite(r)]
+    return {"mean": float(r.mean()), "p99": float(np.percentile(r, 99))}
+
+
 def error_stats(kind, est, ref):
     """Absolute and relative errors (relative as in rel_error) of an estimate: mean, median, max."""
     est = np.asarray(est, np.float64)
@@ -443,6 +450,7 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
     out = sbh.sbh_eval(tree, Q, samples_per_subdomain=S, seed=seed, **kk)
     err_s = float(np.median(rel_error(wl.kernel, out[idx].cpu().numpy(), ref)))
     stats_s = error_stats(wl.kernel, out[idx].cpu().numpy(), ref)
+    tail_s = tail_errors(rel_error(wl.kernel, out[idx].cpu().numpy(), ref))
 
     def timed(fn, reps=3):
         fn()
@@ -459,10 +467,11 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
         return float(np.median(ts))
 
     extra = {}
-    for s2 in (2, 3, 4):
+    for s2 in (2, 3, 4, 8, 16, 32):
         o2 = sbh.sbh_eval(tree, Q, samples_per_subdomain=s2, seed=seed, **kk)
+        r2 = rel_error(wl.kernel, o2[idx].cpu().numpy(), ref)
         extra[f"S{s2}"] = {"ms": timed(lambda: sbh.sbh_eval(tree, Q, samples_per_subdomain=s2, seed=seed, out=o2, **kk), 2),
-                           "median_rel_err": float(np.median(rel_error(wl.kernel, o2[idx].cpu().numpy(), ref)))}
+                           "median_rel_err": float(np.median(r2)), "tail": tail_errors(r2)}
     # the paper's variants (supplemental: roulette off / fixed 1/2; Algorithm 2's uniform path
     # index; identical seeding across queries) and the one-thread-per-query schedule, at S = 1
     variants = {}
@@ -503,6 +512,12 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
         learned["mass_ms_at_equal_error"] = t_mass
         learned["mass_extrapolated"] = extrap_m
         learned["speedup_vs_mass"] = t_mass / learned["ms"]
+        for stat in ("mean", "p99"):  # the same comparison on the mean and the 99th percentile of the errors
+            pts = [(tail_s[stat], eval_ms)] + \
+                  [(v["tail"][stat], v["ms"]) for v in extra.values()]
+            t_m, ex_m = interp_loglog(learned["tail"][stat], [p[0] for p in pts], [p[1] for p in pts])
+            learned[f"speedup_vs_mass_at_equal_{stat}_error"] = t_m / learned["ms"]
+            learned[f"mass_extrapolated_{stat}"] = ex_m
         variants[f"learned_proposal_near{near:g}"] = learned
     for v in list(extra.values()) + list(variants.values()):
         t_bh, extrap, _ = bh_time_at(v["median_rel_err"])
@@ -533,8 +548,9 @@ def learned_proposal(sbh, wl, tree, Q, idx, ref, seed, kk, timed, near):
     train_s = time.perf_counter() - t0
     out = sbh.sbh_eval_learned(tree, net, Q, seed=seed, near=near, **kk)
     ms = timed(lambda: sbh.sbh_eval_learned(tree, net, Q, seed=seed, near=near, out=out, **kk), 2)
-    err = float(np.median(rel_error(wl.kernel, out[idx].cpu().numpy(), ref)))
-    return {"ms": ms, "median_rel_err": err, "near": near, "train_s": train_s,
+    rl = rel_error(wl.kernel, out[idx].cpu().numpy(), ref)
+    err = float(np.median(rl))
+    return {"ms": ms, "median_rel_err": err, "tail": tail_errors(rl), "near": near, "train_s": train_s,
             "train": {"queries": 1024, "adam_steps": 300, "lr": 3e-3, "loss_first": float(losses[0]),
                       "loss_last": float(losses[-1])},
             "scorer": "tensor cores (mma.sync m16n8k16, FP16 operands, FP32 accumulation)"}
