@@ -492,12 +492,15 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
         for theta in (3.0, 2.0, 1.5, 1.2, 1.0, 0.8, 0.67, 0.5, 0.4, 0.3, 0.25):
             ms = timed(lambda: sbh.sbh_eval_bh(tree, Q, theta=theta, warp_vote=vote, out=bh_out, **kk))
             e = sbh.sbh_eval_bh(tree, Qs, theta=theta, warp_vote=vote, **kk).cpu().numpy()
+            re_bh = rel_error(wl.kernel, e, ref)
             sweep.append({"theta": theta, "warp_vote": vote, "ms": ms,
-                          "median_rel_err": float(np.median(rel_error(wl.kernel, e, ref)))})
-    def bh_time_at(err):
+                          "median_rel_err": float(np.median(re_bh)), "tail": tail_errors(re_bh)})
+    def bh_time_at(err, stat="median"):
         best = None
         for vote in (True, False):
-            pts = [(s["median_rel_err"], s["ms"]) for s in sweep if s["warp_vote"] == vote and s["median_rel_err"] > 0]
+            pts = [((s["median_rel_err"] if stat == "median" else s["tail"][stat]), s["ms"])
+                   for s in sweep if s["warp_vote"] == vote]
+            pts = [p for p in pts if p[0] > 0]
             t_bh, extrap = interp_loglog(err, [p[0] for p in pts], [p[1] for p in pts])
             if best is None or t_bh < best[0]:
                 best = (t_bh, extrap, vote)
@@ -518,6 +521,7 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
             t_m, ex_m = interp_loglog(learned["tail"][stat], [p[0] for p in pts], [p[1] for p in pts])
             learned[f"speedup_vs_mass_at_equal_{stat}_error"] = t_m / learned["ms"]
             learned[f"mass_extrapolated_{stat}"] = ex_m
+            learned[f"speedup_vs_bh_at_equal_{stat}_error"] = bh_time_at(learned["tail"][stat], stat)[0] / learned["ms"]
         variants[f"learned_proposal_near{near:g}"] = learned
     for v in list(extra.values()) + list(variants.values()):
         t_bh, extrap, _ = bh_time_at(v["median_rel_err"])
@@ -528,6 +532,8 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
             "bh_sweep": sweep, "bh_tree_build_ms": bh_build_ms,
             "bh_ms_at_equal_error": best[0], "bh_warp_vote": best[2], "extrapolated": best[1],
             "speedup_vs_bh_at_equal_median_error": best[0] / eval_ms,
+            "speedup_vs_bh_at_equal_mean_error": bh_time_at(tail_s["mean"], "mean")[0] / eval_ms,
+            "speedup_vs_bh_at_equal_p99_error": bh_time_at(tail_s["p99"], "p99")[0] / eval_ms,
             "error_reference": "GPU brute force with FP64 tile accumulation on 65536 random queries",
             "time_basis": "evaluation kernels only, trees prebuilt (the paper excludes building)"}
 
