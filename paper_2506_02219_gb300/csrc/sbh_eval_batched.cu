@@ -42,6 +42,11 @@ namespace {
 constexpr int kWarpsPerBlock = 8;
 constexpr int kRing = 64;  // ring capacity per warp; at most 63 tasks wait at any time
 constexpr uint32_t kRingMask = kRing - 1;
+// unroll factor of a swap's loop over pairs of children, measured per kernel: 2 for the terms of
+// one record (Coulomb, affine), 1 for the winding term and its second record. Left to the
+// compiler, the Coulomb instance unrolled further and spilled registers.
+template <int KIND>
+constexpr int swap_unroll() { return KIND == SBH_WINDING ? 1 : 2; }
 
 // per-warp shared state, structure of arrays
 struct WarpState {
@@ -362,8 +367,7 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
         cont = rr_continue(P.rr, unit24(x.y), dT, sdiam[lT], lT, dc, meta_level(mc), p);
         if (cont) {
             prr2 = prr * p;
-            const float pagg = wT / wa;
-            w = 1.0f / (pagg * prr2) / (float)P.S;
+            w = __fdiv_rn(wa, wT * prr2 * (float)P.S);  // 1 / (p_agg p_rr S), p_agg = wT / wa
             if constexpr (LEARNED) wc = wT * (pick_prob < 0.0f ? pc.w / -pick_prob : pick_prob);
             else wc = P.sampling ? (float)(__ldg(&T.ne[child]) - __ldg(&T.nb[child])) : pc.w;
             // a path that reaches a source point stops there: no decision task for it (levels
@@ -527,6 +531,8 @@ __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, Warp
             const float4* cd = KIND == SBH_WINDING ? (st ? S.dip + (f - S.lo) : T.dip + f) : cp;
             float s0 = 0.0f, s1 = 0.0f;
             int k = 0;
+            constexpr int kUnroll = swap_unroll<KIND>();
+#pragma unroll kUnroll
             for (; k + 1 < nc; k += 2) {
                 const float4 p0 = cp[k], p1 = cp[k + 1];
                 if constexpr (KIND == SBH_WINDING) {
@@ -783,14 +789,17 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, SBH_BATCHED_MIN_BLOCKS) k
 {
     __shared__ WarpState s_state[kWarpsPerBlock];
     __shared__ float s_diam[kWarpsPerBlock][kDiamLevels];
+    __shared__ Params s_params[kWarpsPerBlock];  // the warp's current set (kept out of registers)
     const int warp = threadIdx.x >> 5;
     WarpState& W = s_state[warp];
     float* sdiam = s_diam[warp];
+    Params& P = s_params[warp];
     Stage S;
     S.lo = 0; S.n = 0; S.pm = nullptr; S.dip = nullptr; S.cdf = nullptr; S.meta = nullptr; S.fc = nullptr;
-    Params P = M.base;
-    int cur = -1;
     const uint32_t lane = lane_id();
+    if (lane == 0) P = M.base;
+    __syncwarp();
+    int cur = -1;
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0) t = atomicAdd(M.counter, 1ull);
@@ -806,7 +815,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, SBH_BATCHED_MIN_BLOCKS) k
         if (lo != cur) {
             cur = lo;
             const SetDesc& D = M.sets[lo];
-            P.T = D.T; P.Q = D.Q; P.out = D.out; P.nq = D.nq;
+            if (lane == 0) { P.T = D.T; P.Q = D.Q; P.out = D.out; P.nq = D.nq; }
             if (lane < (uint32_t)kDiamLevels) sdiam[lane] = D.T.ctrl->diam[lane];
             __syncwarp();
         }

@@ -110,7 +110,9 @@ __device__ __forceinline__ float dist_rn(float px, float py, float pz, float3 q)
 // p = min(1, max(1, beta~_T) / beta~_c), beta~ = ||q - p~|| / |B|. The child's cell is exactly
 // 4^-(l_c - l_T) times T's, so p = min(1, X / d_c) with X = max(d_T, |B_T|) 4^-(l_c - l_T) (exact),
 // and u < p is u d_c < X, whose sign one FMA gives exactly. rr = 1: p = 1; rr = 2: p = 1/2. On a
-// continue p gets the factor of p_rr, fl(X / d_c) capped at 1.
+// continue p gets the factor of p_rr, X / d_c capped at 1. That factor only scales sample weights,
+// never a decision, so it is the fast quotient (within 2 ulp), exact-rounded only for d_c >= 2^126
+// where the fast one does not hold.
 __device__ __forceinline__ bool rr_continue(int rr, float u, float dT, float BT, uint32_t lT, float dc, uint32_t lc,
                                             float& p)
 {
@@ -118,7 +120,8 @@ __device__ __forceinline__ bool rr_continue(int rr, float u, float dT, float BT,
     if (rr == 2) { p = 0.5f; return u < 0.5f; }
     const float X = fmaxf(dT, BT) * __int_as_float((127 - 2 * (int)(lc - lT)) << 23);
     if (!(fmaf(u, dc, -X) < 0.0f)) return false;
-    p = dc > X ? __fdiv_rn(X, dc) : 1.0f;
+    if (dc <= X) p = 1.0f;
+    else p = dc < 8.5e37f ? __fdividef(X, dc) : __fdiv_rn(X, dc);
     return true;
 }
 
