@@ -45,8 +45,11 @@ constexpr uint32_t kRingMask = kRing - 1;
 // unroll factor of a swap's loop over pairs of children, measured per kernel: 2 for the terms of
 // one record (Coulomb, affine), 1 for the winding term and its second record. Left to the
 // compiler, the Coulomb instance unrolled further and spilled registers.
+#ifndef SBH_SWAP_UNROLL_WINDING
+#define SBH_SWAP_UNROLL_WINDING 1
+#endif
 template <int KIND>
-constexpr int swap_unroll() { return KIND == SBH_WINDING ? 1 : 2; }
+constexpr int swap_unroll() { return KIND == SBH_WINDING ? SBH_SWAP_UNROLL_WINDING : 2; }
 
 // per-warp shared state, structure of arrays
 struct WarpState {
