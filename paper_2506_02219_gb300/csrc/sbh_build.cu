@@ -178,7 +178,26 @@ __global__ void k_bounds(const float* __restrict__ pts, const float* __restrict_
         bad_p += __shfl_xor_sync(0xFFFFFFFFu, bad_p, off);
         bad_w += __shfl_xor_sync(0xFFFFFFFFu, bad_w, off);
     }
+    // then across the block's warps, so that each block adds one set of atomics (not one per warp)
+    __shared__ int s_red[kThreads / 32][8];
+    const int warp = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { s_red[warp][a] = mn[a]; s_red[warp][3 + a] = mx[a]; }
+        s_red[warp][6] = bad_p;
+        s_red[warp][7] = bad_w;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                mn[a] = min(mn[a], s_red[k][a]);
+                mx[a] = max(mx[a], s_red[k][3 + a]);
+            }
+            bad_p += s_red[k][6];
+            bad_w += s_red[k][7];
+        }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             atomicMin(&scratch[a], mn[a]);
@@ -666,30 +685,43 @@ __global__ void k_aggregate(const int32_t* __restrict__ fc, const uint32_t* __re
     }
 }
 
-// FP32 node records, and each node's children's prefix mass fractions (last child = 1)
+// FP32 node records and prefix mass fractions: FP64 quotients rounded once to FP32. FP64 division
+// is slow on this GPU, and a loop of them in one lane holds its whole warp, so each node computes
+// only its own: its centre of mass (a single point, whose quotient m x / m is x itself, copies its
+// own record) and its own fraction among its siblings, the prefix sum of their masses in sibling
+// order over the parent's mass (the same sum, in the same order, as k_aggregate's). (A product
+// with 1 / m is not a substitute for the quotient: small nodes of equal weights often sit exactly
+// on an FP32 rounding midpoint, where the product's last-bit error changes the rounding.)
 __global__ void k_pack(const double* __restrict__ agg, const int32_t* __restrict__ fc,
-                       const uint32_t* __restrict__ meta, const TreeCtrl* __restrict__ ctrl,
-                       float4* __restrict__ pm, float4* __restrict__ dip, float* __restrict__ cdf)
+                       const uint32_t* __restrict__ meta, const int32_t* __restrict__ nb,
+                       const int32_t* __restrict__ parent, const float4* __restrict__ spw,
+                       const float4* __restrict__ snrm, const TreeCtrl* __restrict__ ctrl, float4* __restrict__ pm,
+                       float4* __restrict__ dip, float* __restrict__ cdf)
 {
     const int32_t N = ctrl->depth_base[ctrl->max_depth + 1];
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
-        const double* a = agg + 8 * v;
-        const double m = a[0];
-        pm[v] = make_float4(__double2float_rn(a[1] / m), __double2float_rn(a[2] / m), __double2float_rn(a[3] / m),
-                            __double2float_rn(m));
-        if (dip) dip[v] = make_float4(__double2float_rn(a[4]), __double2float_rn(a[5]), __double2float_rn(a[6]), 0.0f);
-        if (v == 0) cdf[0] = 1.0f;
-        const uint32_t mt = meta[v];
-        const int nc = (int)meta_nchild(mt);
-        if (nc == 0) continue;
-        const int32_t f = fc[v];
-        double tot = 0.0;
-        for (int c = 0; c < nc; ++c) tot += agg[8 * (int64_t)(f + c)];
-        double pre = 0.0;
-        for (int c = 0; c < nc; ++c) {
-            pre += agg[8 * (int64_t)(f + c)];
-            cdf[f + c] = (c == nc - 1) ? 1.0f : __double2float_rn(pre / tot);
+        if (meta_kind(meta[v]) == kPoint) {
+            const float4 p = spw[nb[v]];
+            pm[v] = p;
+            if (dip) {  // m n: one FP32 rounding of the exact product, as the FP64 sum rounded to FP32
+                const float4 q = snrm ? snrm[nb[v]] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                dip[v] = make_float4(__fmul_rn(p.w, q.x), __fmul_rn(p.w, q.y), __fmul_rn(p.w, q.z), 0.0f);
+            }
+        } else {
+            const double* a = agg + 8 * v;
+            const double m = a[0];
+            pm[v] = make_float4(__double2float_rn(a[1] / m), __double2float_rn(a[2] / m),
+                                __double2float_rn(a[3] / m), __double2float_rn(m));
+            if (dip) dip[v] = make_float4(__double2float_rn(a[4]), __double2float_rn(a[5]), __double2float_rn(a[6]), 0.0f);
         }
+        if (v == 0) { cdf[0] = 1.0f; continue; }
+        const int32_t par = parent[v];
+        const int32_t f = fc[par];
+        const int32_t last = f + (int32_t)meta_nchild(meta[par]) - 1;
+        if (v >= last) { cdf[v] = 1.0f; continue; }
+        double pre = 0.0;
+        for (int32_t k = f; k <= v; ++k) pre += agg[8 * (int64_t)k];
+        cdf[v] = __double2float_rn(pre / agg[8 * (int64_t)par]);
     }
 }
 
@@ -890,7 +922,8 @@ cudaError_t build_tree(sbh_tree* T, DeviceTree& D, const uint8_t* lcp, int max_l
         k_aggregate<<<grid_for(n), kThreads, 0, s>>>(D.fc, D.meta, D.nb, T->spw, T->snrm, D.ctrl, gen, D.agg);
         note_launch();
     }
-    k_pack<<<grid_for(2 * n), kThreads, 0, s>>>(D.agg, D.fc, D.meta, D.ctrl, D.pm, D.dip, D.cdf);
+    k_pack<<<grid_for(2 * n), kThreads, 0, s>>>(D.agg, D.fc, D.meta, D.nb, D.parent, T->spw, T->snrm, D.ctrl, D.pm,
+                                                D.dip, D.cdf);
     note_launch();
     k_finalize<<<1, 32, 0, s>>>(D.ctrl, D.fc, D.meta);
     note_launch();
