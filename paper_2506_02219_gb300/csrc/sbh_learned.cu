@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(32 * kTrainWarps) k_loss_grad(const float* __r
         const int nc = (int)(off[s + 1] - r0);
         if (nc < 2 || nc > kMaxLearnedChildren) continue;
         // forward: scores
-        float tsum = 0.0f;
+        float tmax = 0.0f;
         for (int c = 0; c < nc; ++c) {
             const float* x = feats + 6 * (r0 + c);
             float z = b1;
@@ -246,9 +246,15 @@ __global__ void __launch_bounds__(32 * kTrainWarps) k_loss_grad(const float* __r
             float t = w3 * fmaxf(z2, 0.0f);
             for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xFFFFFFFFu, t, o);
             if (lane == 0) sc[warp][c] = t + b3;
-            tsum += targets[r0 + c];
+            tmax = fmaxf(tmax, targets[r0 + c]);
         }
         __syncwarp();
+        // normalised targets t_c / sum_c' t_c', formed as (t_c / t_max) / sum_c' (t_c' / t_max): the
+        // smooth distance's residuals exp(-alpha r) can be FP32 denormals, whose sum has no finite
+        // reciprocal
+        float tsum = 0.0f;
+        if (tmax > 0.0f)
+            for (int c = 0; c < nc; ++c) tsum += targets[r0 + c] / tmax;
         float mx = -3.0e38f;
         for (int c = 0; c < nc; ++c) mx = fmaxf(mx, sc[warp][c]);
         float Z = 0.0f;
@@ -258,7 +264,7 @@ __global__ void __launch_bounds__(32 * kTrainWarps) k_loss_grad(const float* __r
         // backward, recomputing each row's activations
         for (int c = 0; c < nc; ++c) {
             const float* x = feats + 6 * (r0 + c);
-            const float t = tsum > 0.0f ? targets[r0 + c] * tnorm : 1.0f / nc;
+            const float t = tsum > 0.0f ? (targets[r0 + c] / tmax) * tnorm : 1.0f / nc;
             const float lp = sc[warp][c] - mx - logZ;
             if (lane == 0) lsum -= t * lp;
             const float ds = (__expf(lp) - t) * inv_sets;

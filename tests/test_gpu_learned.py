@@ -4,7 +4,8 @@
   accumulation) against the oracle's FP64 network on the same FP16-rounded weights and features:
   the one rounding left, of the hidden activations to FP16 (relative 2^-11), moves a score by at
   most 2^-11 times the network's value on |weights| and |features|; the test allows 1e-3 of it.
-- Training loss and gradient (FP32 master weights) against the oracle's FP64 loss and gradient.
+- Training loss and gradient (FP32 master weights) against the oracle's FP64 loss and gradient,
+  also with targets in the FP32 denormal range (the smooth distance's exp(-alpha r) residuals).
 - Explicit training sets (features and |exact child residual| targets) against the oracle's
   features and brute-force residuals.
 - Unbiasedness: seed-averaged learned estimates (both schedules, gate open everywhere and gated
@@ -58,6 +59,31 @@ def test_loss_grad_matches_oracle(sbh, oracle_mod, sizes):
     assert abs(float(loss.item()) - ref_loss) <= 1e-4 * abs(ref_loss)
     g = grad.cpu().numpy().astype(np.float64)
     assert np.max(np.abs(g - ref_g)) <= 1e-4 * np.max(np.abs(ref_g)), np.max(np.abs(g - ref_g)) / np.max(np.abs(ref_g))
+
+
+def test_loss_grad_for_denormal_targets(sbh, oracle_mod):
+    """The smooth distance's training targets exp(-alpha r) can be FP32 denormals, whose sum has no
+    finite reciprocal. The loss depends only on each set's normalised targets, so targets scaled
+    into the denormal range (1e-40) must give the loss and gradient of the unscaled ones, up to the
+    denormals' rounding."""
+    import torch
+    sizes = [2, 5, 17, 64, 33]
+    rng = np.random.default_rng(12)
+    w = _rand_weights(oracle_mod, 5)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    x = rng.normal(size=(off[-1], 6)).astype(np.float32)
+    t = rng.random(off[-1]).astype(np.float32)
+    tiny = (t.astype(np.float64) * 1e-40).astype(np.float32)
+    sums = [tiny[off[i]:off[i + 1]].astype(np.float64).sum() for i in range(len(sizes))]
+    assert np.all(tiny < np.finfo(np.float32).tiny) and min(sums) < 1.0 / np.finfo(np.float32).max
+    net = sbh.sbh_mlp_create(0)
+    sbh.sbh_mlp_set_weights(net, w)
+    loss, grad = sbh.sbh_mlp_loss_grad(net, dev(x), dev(tiny), torch.from_numpy(off).cuda())
+    ref_loss, ref_g = oracle_mod.mlp_loss_grad(w.astype(np.float64), x.astype(np.float64), t.astype(np.float64), off)
+    g = grad.cpu().numpy().astype(np.float64)
+    assert np.isfinite(float(loss.item())) and np.all(np.isfinite(g))
+    assert abs(float(loss.item()) - ref_loss) <= 1e-3 * abs(ref_loss)
+    assert np.max(np.abs(g - ref_g)) <= 1e-3 * np.max(np.abs(ref_g)), np.max(np.abs(g - ref_g)) / np.max(np.abs(ref_g))
 
 
 def test_weights_round_trip(sbh, oracle_mod):
