@@ -224,8 +224,9 @@ SBH_API sbh_status sbh_mlp_set_state(sbh_mlp* net, const float* host_state, int6
 SBH_API sbh_status sbh_mlp_scores(const sbh_mlp* net, const float* feats, int64_t n, float* scores, void* stream);
 /* Training loss and its gradient in the FP32 master weights: the mean over decision sets s (rows
  * offsets[s] .. offsets[s+1]-1, 2..64 rows each; device int64 offsets) of the cross-entropy between
- * softmax(scores) and the set's targets normalised to sum 1. grad device [SBH_MLP_PARAMS], loss
- * device [1]. */
+ * softmax(scores) and the set's targets (>= 0) normalised to sum 1; a set whose targets are all 0
+ * takes uniform targets. Only each set's ratios matter: targets at any scale, FP32 denormals
+ * included, give the same loss up to their rounding. grad device [SBH_MLP_PARAMS], loss device [1]. */
 SBH_API sbh_status sbh_mlp_loss_grad(sbh_mlp* net, const float* feats, const float* targets, const int64_t* offsets,
                                      int64_t n_sets, float* grad, float* loss, void* stream);
 /* Training rows of explicit decision sets: set s is node set_node[s] at query set_query[s]
