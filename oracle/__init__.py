@@ -61,7 +61,7 @@ class _Kernel(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("sampling", C.c_int32), ("rr", C.c_int32), ("coherent", C.c_int32),
-                ("pad", C.c_int32)]
+                ("abs_mode", C.c_int32)]
 
 
 def _load():
@@ -123,9 +123,9 @@ def kernel(kind: int, softening: float = 1e-3, alpha: float = 200.0, affine=(0.0
     return k
 
 
-def _opts(sampling=SAMPLE_MASS, rr=RR_PAPER, coherent=False) -> _Opts:
+def _opts(sampling=SAMPLE_MASS, rr=RR_PAPER, coherent=False, abs_mode=0) -> _Opts:
     o = _Opts()
-    o.sampling, o.rr, o.coherent, o.pad = int(sampling), int(rr), int(bool(coherent)), 0
+    o.sampling, o.rr, o.coherent, o.abs_mode = int(sampling), int(rr), int(bool(coherent)), int(abs_mode)
     return o
 
 
@@ -221,18 +221,20 @@ class Tree:
 
     def replay(self, queries, S: int = 1, seed: int = 0, kind=COULOMB, softening=1e-3, alpha=200.0,
                affine=(0.0, 0.0, 0.0), sampling=SAMPLE_MASS, rr=RR_PAPER, coherent=False,
-               return_swaps=False, query_index=None, return_abs_sum=False):
+               return_swaps=False, query_index=None, return_abs_sum=False, abs_mode=0):
         """Algorithm 2 replayed with the Philox stream; returns the FP64 estimate of the kernel
         sum per query (the sum of exponentials for the smooth distance kernel). query_index gives
         each query's index in the random stream (default: its position). With return_abs_sum the
         sum of the absolute values of all terms the estimate adds is returned too (the scale of
-        the rounding error of any evaluation of the same signed sum)."""
+        the rounding error of any evaluation of the same signed sum). abs_mode=1 sums instead, for
+        the winding kernel, each term's sensitivity to rounding its node record to FP32,
+        |N| (r + 4 |p|) / (4 pi r^3): the scale that applies where d.N cancels, next to the surface."""
         q = _f32(queries, 3)
         qidx = None if query_index is None else np.ascontiguousarray(np.asarray(query_index, dtype=np.uint32))
         out = np.zeros(q.shape[0], np.float64)
         swaps = np.zeros(q.shape[0], np.int64)
         k = kernel(kind, softening, alpha, affine)
-        o = _opts(sampling, rr, coherent)
+        o = _opts(sampling, rr, coherent, abs_mode)
         absum = np.zeros(q.shape[0], np.float64)
         self._lib.sbho_replay(self._h, C.byref(k), _ptr(q), q.shape[0], int(S), C.c_uint64(seed & (2**64 - 1)),
                               C.byref(o), _ptr(qidx), _ptr(out), _ptr(swaps), _ptr(absum))

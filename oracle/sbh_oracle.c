@@ -601,14 +601,34 @@ static double swap_delta(const otree *t, const sbho_kernel *k, int64_t v, const 
     return s - node_term(t, k, v, q);
 }
 
-/* Magnitude of a swap's terms: sum over children of |m_c f(p_c, q)| plus |m_v f(p_v, q)|. The
- * replay adds these (with the same weights) into abs_sum, the scale against which a computation
- * in lower precision of the same signed sum can be compared. */
-static double swap_abs(const otree *t, const sbho_kernel *k, int64_t v, const double q[3])
+/* Scale of one node term in abs_sum. mode 0: |m f(p~, q)|, the scale of rounding the operations
+ * of a signed sum of these terms. mode 1, for the winding kernel: the term's first-order change
+ * when its record is rounded to FP32 (p~ and N each by a relative eps), divided by eps. With
+ * d = p~ - q and r = |d|, the dot product d.N changes by at most eps (|p~| + r)|N| and r^-3 by a
+ * factor 3 eps |p~| / r, and |d.N| <= r |N|, so the scale is |N| (r + 4 |p~|) / (4 pi r^3). Near
+ * the query d is nearly tangent to the surface and d.N cancels, so this exceeds |term| by far.
+ * Other kernels use mode 0 whatever the mode. */
+static double node_mag(const otree *t, const sbho_kernel *k, int64_t v, const double q[3], int mode)
+{
+    if (mode == 0 || k->kind != K_WINDING) return fabs(node_term(t, k, v, q));
+    const double *p = &t->com[3 * v], *N = &t->dip[3 * v];
+    const double dx = p[0] - q[0], dy = p[1] - q[1], dz = p[2] - q[2];
+    const double r2 = dx * dx + dy * dy + dz * dz;
+    if (r2 == 0.0) return 0.0;
+    const double r = sqrt(r2);
+    const double pn = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);
+    const double nn = sqrt(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+    return nn * (r + 4.0 * pn) / (4.0 * M_PI * r2 * r);
+}
+
+/* Magnitude of a swap's terms: the children's scales plus the node's own (node_mag). The replay
+ * adds these (with the same weights) into abs_sum, the scale against which a computation in lower
+ * precision of the same signed sum can be compared. */
+static double swap_abs(const otree *t, const sbho_kernel *k, int64_t v, const double q[3], int mode)
 {
     double s = 0;
-    for (int c = 0; c < t->nchild[v]; ++c) s += fabs(node_term(t, k, t->first_child[v] + c, q));
-    return s + fabs(node_term(t, k, v, q));
+    for (int c = 0; c < t->nchild[v]; ++c) s += node_mag(t, k, t->first_child[v] + c, q, mode);
+    return s + node_mag(t, k, v, q, mode);
 }
 
 static void node_grad(const otree *t, const sbho_kernel *k, int64_t v, const double q[3], double g[3])
@@ -673,7 +693,7 @@ typedef struct {
     int32_t sampling;   /* SAMPLE_MASS (default) or SAMPLE_COUNT (the paper's uniform index) */
     int32_t rr;         /* RR_PAPER (Eq. 5), RR_OFF, RR_HALF */
     int32_t coherent;   /* 1: every query uses query index 0 in the counter */
-    int32_t pad;
+    int32_t abs_mode;   /* scale of each term in abs_sum (node_mag): 0 |term|, 1 FP32-record sensitivity */
 } sbho_opts;
 
 SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *queries, int64_t nq,
@@ -685,6 +705,7 @@ SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *quer
     const int sampling = opts ? opts->sampling : SAMPLE_MASS;
     const int rr = opts ? opts->rr : RR_PAPER;
     const int coherent = opts ? opts->coherent : 0;
+    const int abs_mode = opts ? opts->abs_mode : 0;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t j = 0; j < nq; ++j) {
         float q32[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
@@ -710,14 +731,14 @@ SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *quer
                     double pagg = p_in(t, T, a, sampling);
                     prr *= (double)p;
                     Fa += delta / (pagg * prr);
-                    Aa += swap_abs(t, k, T, q) / (pagg * prr);
+                    Aa += swap_abs(t, k, T, q, abs_mode) / (pagg * prr);
                     ++swaps;
                     T = c;
                     ++depth;
                 }
             }
             F += CV + Fa / (double)S;
-            A += fabs(CV) + Aa / (double)S;
+            A += node_mag(t, k, a, q, abs_mode) + Aa / (double)S;
         }
         out[j] = F;
         if (nswaps) nswaps[j] = swaps;

@@ -156,3 +156,34 @@ def test_abs_sum_bounds_the_estimate(oracle_mod):
     tp = oracle_mod.Tree(pts, w, d=4)
     est, A = tp.replay(q, seed=1, return_abs_sum=True)
     np.testing.assert_allclose(A, est, rtol=1e-14)
+
+
+
+def test_fp32_record_sensitivity_scale(oracle_mod):
+    """abs_mode=1 scales each winding term by |N| (r + 4 |p|) / (4 pi r^3) >= |term|, so its sum is
+    at least the plain abs_sum; the other kernels ignore the mode. The scale bounds what rounding
+    a node's record (centre of mass and dipole) to FP32 does to its term: at queries on the
+    sources of a surface-sample tree, every internal node's term moves by at most 2^-24 times it."""
+    t, q, F, kw = _setup(oracle_mod, 300, 14, "winding")
+    _, A0 = t.replay(q, S=2, seed=4, return_abs_sum=True, **kw)
+    _, A1 = t.replay(q, S=2, seed=4, return_abs_sum=True, abs_mode=1, **kw)
+    assert np.all(A1 >= A0 * (1 - 1e-12)) and np.any(A1 > 2 * A0)
+    for kind in ("coulomb", "smoothdist"):
+        t2, q2, _, kw2 = _setup(oracle_mod, 300, 14, kind)
+        _, B0 = t2.replay(q2, S=2, seed=4, return_abs_sum=True, **kw2)
+        _, B1 = t2.replay(q2, S=2, seed=4, return_abs_sum=True, abs_mode=1, **kw2)
+        np.testing.assert_array_equal(B0, B1)
+    from paper_2506_02219_gb300 import workloads as W
+    pts, w, nrm = W.shape_union(3000, 5, n_ellipsoids=2, n_boxes=1)
+    e = oracle_mod.Tree(pts, w, nrm, leaf_size=1, d=4).export()
+    inner = e["nchild"] > 0
+    com, dip = e["com"][inner], e["dip"][inner]
+    com32 = com.astype(np.float32).astype(np.float64)
+    dip32 = dip.astype(np.float32).astype(np.float64)
+    for qq in pts[::25].astype(np.float64):
+        d, d32 = com - qq, com32 - qq
+        r, r32 = np.linalg.norm(d, axis=1), np.linalg.norm(d32, axis=1)
+        t64 = (d * dip).sum(1) / (4 * np.pi * r ** 3)
+        t32 = (d32 * dip32).sum(1) / (4 * np.pi * r32 ** 3)
+        scale = np.linalg.norm(dip, axis=1) * (r + 4 * np.linalg.norm(com, axis=1)) / (4 * np.pi * r ** 3)
+        assert np.all(np.abs(t32 - t64) <= 2.0 ** -24 * scale), np.max(np.abs(t32 - t64) / (2.0 ** -24 * scale))
