@@ -52,3 +52,16 @@ def test_committed_profile_matches_the_kernel_sources():
     assert bench.profiled_bytes("winding") is not None
     assert bench.profiled_bytes("winding", "l2_bytes_per_query") is not None
     assert os.path.exists(os.path.join(bench.ROOT, "profiles", "launches_bench_winding.md"))
+
+
+def test_every_hashed_profile_matches_the_kernel_sources():
+    """Each committed ncu summary of a k_stoch_batched instance carries the hash of the kernel
+    sources it was taken on; all must match the sources as they are now."""
+    import glob
+    want = bench.source_hash(bench.EVAL_SOURCES)
+    paths = sorted(glob.glob(os.path.join(bench.ROOT, "profiles", "k_stoch_batched_*.md")))
+    assert len(paths) >= 3
+    for path in paths:
+        first = open(path).readline().strip()
+        assert first.startswith("<!-- source_hash="), path
+        assert first == f"<!-- source_hash={want} -->", path
