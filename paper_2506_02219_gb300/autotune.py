@@ -64,9 +64,17 @@ def autotune(points, weights, queries, kernel: str = "coulomb", normals=None, ta
             table.append({"leaf_size": leaf, "S": S, "schedule": sched, "ms": float(np.median(ts)),
                           "median_rel_err": err})
         tree.free()
+    return {"best": select(table, target_median_rel_err), "table": table}
+
+
+def select(table, target_median_rel_err=None) -> dict:
+    """The configuration to use from measured rows {"ms", "median_rel_err", ...}: with a target,
+    the fastest row that meets it (the most accurate row if none does); without one, the row
+    with the smallest ms x error^2 (the time to reach a fixed error, the error falling as
+    1/sqrt(S)). Ties keep the first row in table order."""
+    if not table:
+        raise ValueError("no measured configuration")
     if target_median_rel_err is not None:
         ok = [r for r in table if r["median_rel_err"] <= target_median_rel_err]
-        best = min(ok, key=lambda r: r["ms"]) if ok else min(table, key=lambda r: r["median_rel_err"])
-    else:
-        best = min(table, key=lambda r: r["ms"] * r["median_rel_err"] ** 2)
-    return {"best": best, "table": table}
+        return min(ok, key=lambda r: r["ms"]) if ok else min(table, key=lambda r: r["median_rel_err"])
+    return min(table, key=lambda r: r["ms"] * r["median_rel_err"] ** 2)
