@@ -159,7 +159,7 @@ SBH_API sbh_status sbh_eval_grad(const sbh_tree* tree, const float* queries, int
 /* One-shot build and evaluation from HOST buffers (the call for callers without device memory
  * of their own): points [n][3], weights [n], normals [n][3] or NULL, queries [nq][3] and out [nq] are
  * host memory. The points go up and the tree is built (as sbh_build) while the queries go up chunk
- * by chunk (chunk queries each, rounded up to a multiple of 32; 0 = max(2^24, nq / 4)) on a copy
+ * by chunk (chunk queries each, rounded up to a multiple of 32; 0 = half of nq from 2^22 on, else nq) on a copy
  * stream; each chunk is evaluated
  * (as sbh_eval, with the random stream of its place in the whole set, so out equals sbh_eval on
  * all queries bit for bit) as soon as it has landed, and its results come back on a second copy

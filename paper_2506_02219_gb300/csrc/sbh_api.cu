@@ -233,9 +233,11 @@ sbh_status sbh_solve_host(const float* points, const float* weights, const float
     sbh_eval_opts o = {0, 0, 0, 0, 0};
     if (opts) o = *opts;
     if (!opts_ok(o)) return fail(SBH_EINVAL, "sbh_eval_opts out of range");
-    // each chunk adds a launch tail (~0.15 ms); uploads are overlapped with the build anyway, so
-    // only very large query sets are split (their downloads then overlap the next chunk)
-    if (chunk == 0) chunk = std::max<int64_t>(int64_t(1) << 24, (nq + 3) / 4);
+    // each chunk adds a launch tail (~0.15 ms), but the first chunk's evaluation starts after half
+    // of the query upload (which outlasts the build where the host link is slow) and its download
+    // overlaps the second chunk: two chunks from 2^22 queries on (measured even where the link is
+    // fast: 29.20 ms for one or two chunks at 2^24 queries)
+    if (chunk == 0) chunk = nq >= (int64_t(1) << 22) ? (nq + 1) / 2 : std::max<int64_t>(nq, 1);
     // whole 32-query tiles: a tile's results depend on its queries only, so the chunks' tiles must
     // be those of one launch over all queries
     chunk = (chunk + 31) / 32 * 32;
