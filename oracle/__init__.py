@@ -9,8 +9,10 @@ queries); this module compiles it with the host C compiler and marshals numpy ar
 
 Functions and the passages they follow:
   brute(...)        Eq. 1, the exact kernel sum.
-  Tree(...)         Sec. 3.1, the octree-like tree with aggregate mass and centre of mass.
-  Tree.bh(...)      Algorithm 1 (Barnes-Hut), Eq. 2.
+  Tree(...)         Sec. 3.1, the octree-like tree with aggregate mass and centre of mass. The
+                    options box=, collapse= and subdomain_generation= select alternative readings
+                    of Sec. 3.1 and Sec. 3.3.1 (oracle only; the CUDA path implements the default).
+  Tree.bh(...)      Algorithm 1 (Barnes-Hut), Eq. 2; Tree.bh_work counts its node tests and terms.
   Tree.replay(...)  Algorithm 2 with Eq. 5 (Russian roulette), Eq. 6 (swap), Eq. 7 (estimator),
                     driven by the same counter-based Philox4x32-10 stream as the GPU kernel.
   Tree.enumerate()  exact mean and variance of Eq. 7 by enumeration (Appendix A).
@@ -77,13 +79,16 @@ def _load():
         lib.sbho_brute.argtypes = [C.POINTER(_Kernel), P, P, P, i64, P, i64, P]
         lib.sbho_tree_build.argtypes = [P, P, P, i64, i32, i32]
         lib.sbho_tree_build.restype = P
+        lib.sbho_tree_build_ex.argtypes = [P, P, P, i64, i32, i32, i32, i32, i32]
+        lib.sbho_tree_build_ex.restype = P
+        lib.sbho_bh_work.argtypes = [P, P, i64, C.c_float, P]
         lib.sbho_tree_free.argtypes = [P]
         lib.sbho_tree_nnodes.argtypes = [P]
         lib.sbho_tree_nnodes.restype = i64
         lib.sbho_tree_meta.argtypes = [P, P, P]
         lib.sbho_tree_export.argtypes = [P] + [P] * 11
         lib.sbho_bh.argtypes = [P, C.POINTER(_Kernel), P, i64, C.c_float, P]
-        lib.sbho_replay.argtypes = [P, C.POINTER(_Kernel), P, i64, i32, u64, C.POINTER(_Opts), P, P, P, P]
+        lib.sbho_replay.argtypes = [P, C.POINTER(_Kernel), P, i64, i32, u64, C.POINTER(_Opts), P, P, P, P, P]
         lib.sbho_enumerate.argtypes = [P, C.POINTER(_Kernel), P, i64, C.POINTER(_Opts), P, P]
         lib.sbho_brute_grad.argtypes = [C.POINTER(_Kernel), P, P, P, i64, P, i64, P]
         lib.sbho_replay_grad.argtypes = [P, C.POINTER(_Kernel), P, P, i64, i32, u64, C.POINTER(_Opts), P, P, P, P]
@@ -164,18 +169,37 @@ def brute_grad(points, weights, queries, kind=COULOMB, normals=None, softening=1
     return out
 
 
-class Tree:
-    """The oracle's tree over (points, weights[, normals]) with per-dimension branching d."""
+BOX_MODES = {"cell": 0, "tight": 1, "tight_literal": 2}
 
-    def __init__(self, points, weights, normals=None, leaf_size: int = 1, d: int = 4):
+
+class Tree:
+    """The oracle's tree over (points, weights[, normals]) with per-dimension branching d.
+
+    The defaults are the readings the CUDA path implements. The other settings exist in the
+    oracle alone, to measure what each reading of the paper does to the estimator:
+      box="cell"           |B_a| = diagonal of the node's octree cell (default)
+      box="tight"          |B_a| = diagonal of the tight box of the node's points (Sec. 3.1's
+                           wording); a node of zero extent takes its cell's diagonal
+      box="tight_literal"  the tight box everywhere: Eq. 5 gives p = 0 into one-point nodes, so
+                           the estimator never takes the swaps above them (it is truncated)
+      collapse=False       single-child chains are kept as nodes (default: they collapse)
+      subdomain_generation=g  subdomains are the nodes g generations below the root, plus any
+                           leaf above that (default 1: the root's children, Sec. 3.3.1)
+    """
+
+    def __init__(self, points, weights, normals=None, leaf_size: int = 1, d: int = 4, box: str = "cell",
+                 collapse: bool = True, subdomain_generation: int = 1):
         lib = _load()
         self.points = _f32(points, 3)
         self.weights = _f32(weights)
         self.normals = _f32(normals, 3)
         self.n = self.points.shape[0]
         self.d = d
-        h = lib.sbho_tree_build(_ptr(self.points), _ptr(self.weights), _ptr(self.normals), self.n,
-                                int(leaf_size), int(d))
+        if box not in BOX_MODES:
+            raise ValueError(f"box must be one of {sorted(BOX_MODES)}")
+        h = lib.sbho_tree_build_ex(_ptr(self.points), _ptr(self.weights), _ptr(self.normals), self.n,
+                                   int(leaf_size), int(d), BOX_MODES[box], int(bool(collapse)),
+                                   int(subdomain_generation))
         if not h:
             raise ValueError("oracle tree build rejected its inputs")
         self._h = h
@@ -219,16 +243,26 @@ class Tree:
         self._lib.sbho_bh(self._h, C.byref(k), _ptr(q), q.shape[0], C.c_float(beta), _ptr(out))
         return out
 
+    def bh_work(self, queries, beta: float) -> np.ndarray:
+        """Algorithm 1's work per query: far-field tests of the nodes it opens plus the terms it
+        adds (int64)."""
+        q = _f32(queries, 3)
+        out = np.zeros(q.shape[0], np.int64)
+        self._lib.sbho_bh_work(self._h, _ptr(q), q.shape[0], C.c_float(beta), _ptr(out))
+        return out
+
     def replay(self, queries, S: int = 1, seed: int = 0, kind=COULOMB, softening=1e-3, alpha=200.0,
                affine=(0.0, 0.0, 0.0), sampling=SAMPLE_MASS, rr=RR_PAPER, coherent=False,
-               return_swaps=False, query_index=None, return_abs_sum=False, abs_mode=0):
+               return_swaps=False, query_index=None, return_abs_sum=False, abs_mode=0, return_terms=False):
         """Algorithm 2 replayed with the Philox stream; returns the FP64 estimate of the kernel
         sum per query (the sum of exponentials for the smooth distance kernel). query_index gives
         each query's index in the random stream (default: its position). With return_abs_sum the
         sum of the absolute values of all terms the estimate adds is returned too (the scale of
         the rounding error of any evaluation of the same signed sum). abs_mode=1 sums instead, for
         the winding kernel, each term's sensitivity to rounding its node record to FP32,
-        |N| (r + 4 |p|) / (4 pi r^3): the scale that applies where d.N cancels, next to the surface."""
+        |N| (r + 4 |p|) / (4 pi r^3): the scale that applies where d.N cancels, next to the surface.
+        return_terms adds the number of kernel terms evaluated per query (control variates plus
+        every swap's children and node)."""
         q = _f32(queries, 3)
         qidx = None if query_index is None else np.ascontiguousarray(np.asarray(query_index, dtype=np.uint32))
         out = np.zeros(q.shape[0], np.float64)
@@ -236,13 +270,16 @@ class Tree:
         k = kernel(kind, softening, alpha, affine)
         o = _opts(sampling, rr, coherent, abs_mode)
         absum = np.zeros(q.shape[0], np.float64)
+        terms = np.zeros(q.shape[0], np.int64)
         self._lib.sbho_replay(self._h, C.byref(k), _ptr(q), q.shape[0], int(S), C.c_uint64(seed & (2**64 - 1)),
-                              C.byref(o), _ptr(qidx), _ptr(out), _ptr(swaps), _ptr(absum))
+                              C.byref(o), _ptr(qidx), _ptr(out), _ptr(swaps), _ptr(absum), _ptr(terms))
         res = (out,)
         if return_swaps:
             res += (swaps,)
         if return_abs_sum:
             res += (absum,)
+        if return_terms:
+            res += (terms,)
         return res if len(res) > 1 else out
 
     def replay_grad(self, queries, S: int = 1, seed: int = 0, kind=COULOMB, softening=1e-3, alpha=200.0,

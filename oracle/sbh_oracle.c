@@ -29,6 +29,14 @@
  *   - |B_a| is the diagonal of the node's octree cell, sqrt(3) * side * d^-level.
  *   - A node whose points all fall in one child cell is replaced by that child (single-child
  *     chains collapse); the kept node keeps its own level.
+ *   - The subdomains are the root's children (Sec. 3.3.1).
+ *   Three alternatives are kept as build options of the oracle alone, to measure what each
+ *   reading does to the estimator (sbho_tree_build_ex): |B_a| as the diagonal of the tight
+ *   axis-aligned box of the node's points (Sec. 3.1's wording), with zero-extent nodes taking
+ *   their cell's diagonal (box mode 1) or literally 0, so that Eq. 5 gives p = 0 into one-point
+ *   nodes and the estimator is truncated there (box mode 2); single-child chains kept as nodes;
+ *   and the subdomains taken one or more generations deeper ("other choices are also possible",
+ *   Sec. 3.3.1).
  *   - A node is a leaf when it holds <= leaf_size points or sits at the deepest level; a leaf
  *     with more than one point has its points as children, one level deeper.
  *   - The path index I is drawn lazily, one child per level, child c of T with probability
@@ -242,6 +250,10 @@ typedef struct {
     float *mass32, *com32, *cdf;   /* FP32 roundings used by the FP32 decisions: [N], [3N], [N] */
     int64_t n_sub;                 /* subdomains (Sec. 3.3.1): the root's children, or the root */
     int64_t first_sub;
+    int64_t *subs;                 /* [n_sub] subdomain node ids */
+    int32_t box_mode;              /* |B_a|: 0 cell diagonal, 1 tight box (cell if zero extent), 2 tight box */
+    int32_t collapse;              /* 1: single-child chains collapse */
+    double *bd;                    /* [N] |B_a| in FP64 for box modes 1 and 2 */
 } otree;
 
 /* Quantise one coordinate to a 20-bit cell index: floor((x - lo) * (2^20 / side)), clamped.
@@ -317,7 +329,13 @@ static tnode *make_node(const otree *t, int64_t b, int64_t e, int level)
         int runs = 1;
         for (int64_t i = b + 1; i < e; ++i)
             if (digit_at(t, t->code[i], x->level + 1) != digit_at(t, t->code[i - 1], x->level + 1)) ++runs;
-        if (runs == 1) { x->level += 1; continue; }  /* single child: collapse into it */
+        if (runs == 1 && t->collapse) { x->level += 1; continue; }  /* single child: collapse into it */
+        if (runs == 1) {  /* single child kept as a node one level down (collapse off) */
+            x->nchild = 1;
+            x->child = (tnode **)calloc(1, sizeof(tnode *));
+            x->child[0] = make_node(t, b, e, x->level + 1);
+            return x;
+        }
         x->nchild = runs;
         x->child = (tnode **)calloc((size_t)runs, sizeof(tnode *));
         int64_t s = b; int c = 0;
@@ -345,13 +363,21 @@ static int64_t count_tnodes(const tnode *x)
     return c;
 }
 
-SBHO_API void *sbho_tree_build(const float *pts, const float *w, const float *nrm, int64_t n,
-                               int32_t leaf_size, int32_t d)
+/* The tree with the default readings when box_mode = 0, collapse = 1, sub_gen = 1. Otherwise:
+ * box_mode 1 or 2 takes |B_a| from the tight box of the node's points (see the file header),
+ * collapse = 0 keeps single-child chains, and sub_gen = g takes as subdomains the nodes g
+ * generations below the root (and any leaf above that generation), which still cover every
+ * point once, as Sec. 3.3.1 requires. */
+SBHO_API void *sbho_tree_build_ex(const float *pts, const float *w, const float *nrm, int64_t n,
+                                  int32_t leaf_size, int32_t d, int32_t box_mode, int32_t collapse,
+                                  int32_t sub_gen)
 {
     if (n < 1 || leaf_size < 1 || (d != 2 && d != 4)) return NULL;
+    if (box_mode < 0 || box_mode > 2 || sub_gen < 1) return NULL;
     otree *t = (otree *)calloc(1, sizeof(otree));
     t->n = n; t->d = d; t->bits = (d == 4) ? 6 : 3; t->max_level = 60 / t->bits;
     t->leaf_size = leaf_size; t->has_normals = nrm != NULL;
+    t->box_mode = box_mode; t->collapse = collapse != 0;
 
     /* root cube: lower corner = per-axis minimum, edge = largest extent (1 if all coincide) */
     float mn[3], mx[3];
@@ -457,7 +483,47 @@ SBHO_API void *sbho_tree_build(const float *pts, const float *w, const float *nr
     }
     if (t->nchild[0] > 0) { t->first_sub = t->first_child[0]; t->n_sub = t->nchild[0]; }
     else { t->first_sub = 0; t->n_sub = 1; }
+
+    /* subdomains: generation sub_gen below the root, plus the leaves above it */
+    t->subs = (int64_t *)malloc((size_t)N * sizeof(int64_t));
+    if (N == 1) {
+        t->subs[0] = 0; t->n_sub = 1;
+    } else {
+        int32_t *gen = (int32_t *)calloc((size_t)N, sizeof(int32_t));
+        t->n_sub = 0;
+        for (int64_t v = 1; v < N; ++v) {
+            gen[v] = gen[t->parent[v]] + 1;
+            if (gen[v] == sub_gen || (gen[v] < sub_gen && t->nchild[v] == 0)) t->subs[t->n_sub++] = v;
+        }
+        free(gen);
+        t->first_sub = t->subs[0];
+    }
+
+    /* |B_a| of the tight box of each node's points, for box modes 1 and 2 */
+    if (box_mode != 0) {
+        t->bd = (double *)malloc((size_t)N * sizeof(double));
+        for (int64_t v = 0; v < N; ++v) {
+            double lo[3], hi[3], s2 = 0.0;
+            for (int a = 0; a < 3; ++a) { lo[a] = INFINITY; hi[a] = -INFINITY; }
+            for (int64_t i = t->begin[v]; i < t->end[v]; ++i)
+                for (int a = 0; a < 3; ++a) {
+                    double x = pts[3 * t->perm[i] + a];
+                    if (x < lo[a]) lo[a] = x;
+                    if (x > hi[a]) hi[a] = x;
+                }
+            for (int a = 0; a < 3; ++a) s2 += (hi[a] - lo[a]) * (hi[a] - lo[a]);
+            double b = sqrt(s2);
+            if (b == 0.0 && box_mode == 1) b = ldexp(sqrt(3.0) * t->side, -(t->bits / 3) * t->level[v]);
+            t->bd[v] = b;
+        }
+    }
     return t;
+}
+
+SBHO_API void *sbho_tree_build(const float *pts, const float *w, const float *nrm, int64_t n,
+                               int32_t leaf_size, int32_t d)
+{
+    return sbho_tree_build_ex(pts, w, nrm, n, leaf_size, d, 0, 1, 1);
 }
 
 SBHO_API void sbho_tree_free(void *h)
@@ -466,7 +532,7 @@ SBHO_API void sbho_tree_free(void *h)
     if (!t) return;
     free(t->perm); free(t->code); free(t->begin); free(t->end); free(t->first_child);
     free(t->parent); free(t->nchild); free(t->level); free(t->mass); free(t->com); free(t->dip);
-    free(t->mass32); free(t->com32); free(t->cdf);
+    free(t->mass32); free(t->com32); free(t->cdf); free(t->subs); free(t->bd);
     free(t);
 }
 
@@ -526,7 +592,20 @@ static float dist32(const float p[3], const float q[3])
 /* far-field ratio beta~ = ||q - p_a|| / |B_a| (Sec. 3.3), FP32 */
 static float ffratio32(const otree *t, int64_t v, const float q[3])
 {
+    if (t->box_mode != 0) return dist32(&t->com32[3 * v], q) / (float)t->bd[v];  /* inf at |B| = 0 */
     return dist32(&t->com32[3 * v], q) / diam32(t, t->level[v]);
+}
+
+/* Eq. 5 with |B| from the tight boxes (box modes 1, 2), in FP64: p = min(1, max(1, d_v/B_v) /
+ * (d_c/B_c)); d_c = 0 gives 1, and B_c = 0 < d_c gives 0 (beta~_c infinite). */
+static double rr_prob_box(const otree *t, int64_t v, int64_t c, double dv, double dc)
+{
+    if (dc == 0.0) return 1.0;
+    if (t->bd[c] == 0.0) return 0.0;
+    double bt = dv / t->bd[v];
+    double num = bt > 1.0 ? bt : 1.0;
+    double r = num / (dc / t->bd[c]);
+    return r < 1.0 ? r : 1.0;
 }
 
 /* Eq. 5 for the step from node v into its child c with the draw u: the path continues iff u < p,
@@ -539,6 +618,12 @@ static int rr_continue32(const otree *t, int64_t v, int64_t c, const float q[3],
 {
     if (rr == RR_OFF) { *p = 1.0f; return 1; }
     if (rr == RR_HALF) { *p = 0.5f; return u < 0.5f; }
+    if (t->box_mode != 0) {
+        double pb = rr_prob_box(t, v, c, dist32(&t->com32[3 * v], q), dist32(&t->com32[3 * c], q));
+        if (!((double)u < pb)) return 0;
+        *p = (float)pb;
+        return 1;
+    }
     float dv = dist32(&t->com32[3 * v], q), dc = dist32(&t->com32[3 * c], q);
     float bv = diam32(t, t->level[v]);
     float X = ldexpf(dv > bv ? dv : bv, -(t->bits / 3) * (t->level[c] - t->level[v]));
@@ -557,6 +642,7 @@ static double rr_prob64(const otree *t, int64_t v, int64_t c, const double q[3],
         double x = t->com[3 * v + a] - q[a], y = t->com[3 * c + a] - q[a];
         dv += x * x; dc += y * y;
     }
+    if (t->box_mode != 0) return rr_prob_box(t, v, c, sqrt(dv), sqrt(dc));
     double bt = sqrt(dv) / ldexp(sqrt(3.0) * t->side, -(t->bits / 3) * t->level[v]);
     double bc = sqrt(dc) / ldexp(sqrt(3.0) * t->side, -(t->bits / 3) * t->level[c]);
     double num = bt > 1.0 ? bt : 1.0;
@@ -662,6 +748,25 @@ static double bh_rec(const otree *t, const sbho_kernel *k, int64_t v, const doub
     return F;
 }
 
+/* Algorithm 1's work at one query: the far-field tests of opened nodes plus the accepted terms */
+static int64_t bh_work(const otree *t, int64_t v, const float q32[3], float beta)
+{
+    if (t->nchild[v] == 0 || ffratio32(t, v, q32) >= beta) return 1;
+    int64_t w = 1;
+    for (int c = 0; c < t->nchild[v]; ++c) w += bh_work(t, t->first_child[v] + c, q32, beta);
+    return w;
+}
+
+SBHO_API void sbho_bh_work(const void *h, const float *queries, int64_t nq, float beta, int64_t *out)
+{
+    const otree *t = (const otree *)h;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t j = 0; j < nq; ++j) {
+        float q32[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
+        out[j] = bh_work(t, 0, q32, beta);
+    }
+}
+
 SBHO_API void sbho_bh(const void *h, const sbho_kernel *k, const float *queries, int64_t nq,
                       float beta, double *out)
 {
@@ -698,7 +803,7 @@ typedef struct {
 
 SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *queries, int64_t nq,
                           int32_t S, uint64_t seed, const sbho_opts *opts, const uint32_t *qidx,
-                          double *out, int64_t *nswaps, double *abs_sum)
+                          double *out, int64_t *nswaps, double *abs_sum, int64_t *nterms)
 {
     const otree *t = (const otree *)h;
     const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
@@ -711,9 +816,9 @@ SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *quer
         float q32[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
         double q[3] = {q32[0], q32[1], q32[2]};
         double F = 0, A = 0;
-        int64_t swaps = 0;
+        int64_t swaps = 0, terms = t->n_sub;  /* one control variate per subdomain */
         for (int64_t ai = 0; ai < t->n_sub; ++ai) {
-            int64_t a = t->first_sub + ai;
+            int64_t a = t->subs[ai];
             double CV = node_term(t, k, a, q);
             double Fa = 0, Aa = 0;
             for (int32_t s = 0; s < S; ++s) {
@@ -733,6 +838,7 @@ SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *quer
                     Fa += delta / (pagg * prr);
                     Aa += swap_abs(t, k, T, q, abs_mode) / (pagg * prr);
                     ++swaps;
+                    terms += t->nchild[T] + 1;
                     T = c;
                     ++depth;
                 }
@@ -743,6 +849,7 @@ SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *quer
         out[j] = F;
         if (nswaps) nswaps[j] = swaps;
         if (abs_sum) abs_sum[j] = A;
+        if (nterms) nterms[j] = terms;
     }
 }
 
@@ -768,7 +875,7 @@ SBHO_API void sbho_replay_grad(const void *h, const sbho_kernel *k, const float 
         double q[3] = {q_val[3 * j], q_val[3 * j + 1], q_val[3 * j + 2]};
         double F = 0, G[3] = {0, 0, 0}, A = 0, g[3];
         for (int64_t ai = 0; ai < t->n_sub; ++ai) {
-            int64_t a = t->first_sub + ai;
+            int64_t a = t->subs[ai];
             F += node_term(t, k, a, q);
             node_grad(t, k, a, q, g);
             for (int c = 0; c < 3; ++c) { G[c] += g[c]; A += fabs(g[c]); }
@@ -823,6 +930,7 @@ static void enum_grad_rec(const otree *t, const sbho_kernel *k, int64_t a, int64
         double pi = w / tot;
         double p = rr_prob64(t, T, ch, q, rr);
         double prr2 = prr * p;
+        if (!(p > 0.0)) continue;
         /* this path continues with probability P pi p and then carries the swap term */
         for (int d = 0; d < 3; ++d) acc[d] += P * pi * p * g[d] / (pagg * prr2);
         enum_grad_rec(t, k, a, ch, q, P * pi * p, prr2, sampling, rr, acc);
@@ -839,7 +947,7 @@ SBHO_API void sbho_enumerate_grad(const void *h, const sbho_kernel *k, const flo
         double q[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
         double E[3] = {0, 0, 0}, g[3];
         for (int64_t ai = 0; ai < t->n_sub; ++ai) {
-            int64_t a = t->first_sub + ai;
+            int64_t a = t->subs[ai];
             node_grad(t, k, a, q, g);
             for (int d = 0; d < 3; ++d) E[d] += g[d];
             enum_grad_rec(t, k, a, a, q, 1.0, 1.0, sampling, rr, E);
@@ -1025,7 +1133,7 @@ static void enum_learned_rec(const otree *t, const sbho_kernel *k, const double 
         acc->e1 += Pstop * V;
         acc->e2 += Pstop * V * V;
         double prr2 = prr * p;
-        enum_learned_rec(t, k, w, eps, near, ch, q, q32, P * pi[c] * p, V + delta / (ppath * prr2), ppath * pi[c],
+        if (p > 0.0) enum_learned_rec(t, k, w, eps, near, ch, q, q32, P * pi[c] * p, V + delta / (ppath * prr2), ppath * pi[c],
                          prr2, acc);
     }
     free(pi);
@@ -1040,7 +1148,7 @@ SBHO_API void sbho_enumerate_learned(const void *h, const sbho_kernel *k, const 
         const float *q32 = &queries[3 * j];
         double E = 0, Var = 0;
         for (int64_t ai = 0; ai < t->n_sub; ++ai) {
-            int64_t a = t->first_sub + ai;
+            int64_t a = t->subs[ai];
             moments m = {0, 0};
             enum_learned_rec(t, k, w, eps, near, a, q, q32, 1.0, 0.0, 1.0, 1.0, &m);
             E += node_term(t, k, a, q) + m.e1;
@@ -1078,7 +1186,7 @@ static void enum_rec(const otree *t, const sbho_kernel *k, int64_t a, int64_t T,
         acc->e1 += Pstop * V;
         acc->e2 += Pstop * V * V;
         double prr2 = prr * p;
-        enum_rec(t, k, a, ch, q, P * pi * p, V + delta / (pagg * prr2), prr2, sampling, rr, acc);
+        if (p > 0.0) enum_rec(t, k, a, ch, q, P * pi * p, V + delta / (pagg * prr2), prr2, sampling, rr, acc);
     }
 }
 
@@ -1093,7 +1201,7 @@ SBHO_API void sbho_enumerate(const void *h, const sbho_kernel *k, const float *q
         double q[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
         double E = 0, Var = 0;
         for (int64_t ai = 0; ai < t->n_sub; ++ai) {
-            int64_t a = t->first_sub + ai;
+            int64_t a = t->subs[ai];
             moments m = {0, 0};
             enum_rec(t, k, a, a, q, 1.0, 0.0, 1.0, sampling, rr, &m);
             E += node_term(t, k, a, q) + m.e1;

@@ -32,9 +32,14 @@ MUTATIONS = {
         "((uint64_t)((cx >> b) & 1u) << 2) | ((uint64_t)((cy >> b) & 1u) << 1) |",
         "((uint64_t)((cy >> b) & 1u) << 2) | ((uint64_t)((cx >> b) & 1u) << 1) |"),
     "single-child chains kept": (
-        "if (runs == 1) { x->level += 1; continue; }",
-        "if (runs == 1) { x->nchild = 1; x->child = (tnode **)calloc(1, sizeof(tnode *)); "
-        "x->child[0] = make_node(t, b, e, x->level + 1); return x; }"),
+        "if (runs == 1 && t->collapse) { x->level += 1; continue; }",
+        "if (runs == 1 && !t->collapse) { x->level += 1; continue; }"),
+    "tight box without the zero-extent rule": ("if (b == 0.0 && box_mode == 1) b = ldexp(",
+                                               "if (b == 0.0 && box_mode == 3) b = ldexp("),
+    "tight box radius for its diameter": ("double b = sqrt(s2);", "double b = 0.5 * sqrt(s2);"),
+    "subdomains one generation too deep": (
+        "if (gen[v] == sub_gen || (gen[v] < sub_gen && t->nchild[v] == 0))",
+        "if (gen[v] == sub_gen + 1 || (gen[v] < sub_gen + 1 && t->nchild[v] == 0))"),
     "Philox key schedule": ("if (round > 0) { k0 += weyl0; k1 += weyl1; }",
                             "if (round > 1) { k0 += weyl0; k1 += weyl1; }"),
     "winding gradient missing its r^-5 term": (
@@ -56,7 +61,7 @@ def test_pins_catch_planted_mistake(tmp_path, name):
     assert src in text, "mutation anchor not found"
     c.write_text(text.replace(src, dst, 1))
     tests = [f"tests/{f}" for f in ("test_oracle_philox.py", "test_oracle_brute.py", "test_oracle_tree.py",
-                                    "test_oracle_estimator.py", "test_oracle_grad.py")]
+                                    "test_oracle_estimator.py", "test_oracle_grad.py", "test_oracle_readings.py")]
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *tests],
                        cwd=tmp_path, capture_output=True, text=True, timeout=900)
     assert r.returncode == 1, f"pins did not catch: {name}\n{r.stdout[-2000:]}"
