@@ -57,8 +57,27 @@ def flush_l2(dev):
 # 2 mul + accumulate; smooth distance 3 sub + r^2 (2 FMA + mul) + r (rsqrt, mul) + compare +
 # alpha (d - ref) (sub, mul) + exp + FMA; affine 3 sub + g.(p - q) (2 FMA + mul) + add + mul + add.
 FLOPS_PER_TERM = {"coulomb": 12, "winding": 19, "smoothdist": 16, "affine": 11}
-# FP32 lanes per SM and SMs of a GB300: 128 x 152, two flops per lane per cycle (FMA)
-FP32_LANES = 152 * 128
+# FP32 lanes per SM of a Blackwell SM (two flops per lane per cycle with an FMA); the SM count is
+# read from the device and the clock from the samples taken during the timed region
+FP32_LANES_PER_SM = 128
+
+
+def fp32_peak_tflops(sms: int, sm_mhz: float) -> float:
+    """Dense FP32 FMA peak: SMs x 128 lanes x 2 flop x clock."""
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+def peak_clock_mhz(clk):
+    """The SM clock the peak is taken at: the maximum SM clock nvidia-smi reported while the timed
+    region ran (clocks.max.sm); else the measured one in MEASURED_PEAKS.json; else the
+    GB300's nominal maximum. Returns (MHz, where it came from)."""
+    if clk and clk.get("sm_max_mhz"):
+        return float(clk["sm_max_mhz"]), "clocks.max.sm sampled during the timed region"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+    except (OSError, KeyError, ValueError):
+        return 2070.0, "nominal maximum SM clock of a GB300 (no sample)"
 
 
 def workload_by_name(name: str, rank: int = 0):
@@ -66,6 +85,8 @@ def workload_by_name(name: str, rank: int = 0):
     b = W.BASE_SEED
     if name == "winding":
         return W.winding_ellipsoids(seed=b + 1 + 1000 * rank)
+    if name == "winding_random":
+        return W.winding_ellipsoids_random(seed=b + 1 + 1000 * rank)
     if name == "cube":
         return W.coulomb_cube(seed=b + 0 + 1000 * rank)
     if name == "slice_coulomb":
@@ -261,6 +282,25 @@ def measured_hbm_gbs():
         return None
 
 
+def timed_ms(fn, dev, reps=3):
+    """Median event-timed duration (ms) of fn on the current stream, after one untimed call, with
+    L2 flushed (outside the events) before every timed call."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        flush_l2(dev)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
 # ------------------------------------------------------------------------------------------------
 # CPU oracle timing (the cpu_baseline leg and the reference arm)
 # ------------------------------------------------------------------------------------------------
@@ -403,8 +443,9 @@ def run_ours(args):
         cnt = sbh.sbh_eval_count(tree, Q, samples_per_subdomain=S, seed=seed, **kk)
         c = np.array([cnt["terms"], cnt["records"], cnt["decisions"], cnt["cdf_reads"]], np.float64)
         flops = c[0] * FLOPS_PER_TERM[wl.kernel]
-        sm_mhz = 2070.0
-        peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+        sms = int(torch.cuda.get_device_properties(dev).multi_processor_count)
+        sm_mhz, clk_src = peak_clock_mhz(clk)
+        peak = fp32_peak_tflops(sms, sm_mhz)
         achieved = flops / (eval_ms / 1e3) / 1e12
         traffic_pq = profiled_bytes(args.workload)
         l2_pq = profiled_bytes(args.workload, "l2_bytes_per_query")
@@ -420,11 +461,18 @@ def run_ours(args):
         result["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                               "frac": achieved / peak,
                               "traffic": (traffic_pq * nq) if traffic_pq is not None else None,
+                              "traffic_source": (f"ncu capture summarised in profiles/k_stoch_batched_{args.workload}.md "
+                                                 f"(dram__bytes_read.sum + dram__bytes_write.sum per query x queries), "
+                                                 f"used because its kernel-source hash {source_hash(EVAL_SOURCES)} "
+                                                 f"matches this build") if traffic_pq is not None else
+                                                "none: no ncu capture of this kernel source",
                               "memory": memory,
                               "kernel": "k_stoch_batched", "terms_per_query": c[0] / nq,
                               "records_per_query": c[1] / nq, "decisions_per_query": c[2] / nq,
                               "flops_per_term": FLOPS_PER_TERM[wl.kernel],
-                              "peak_basis": "152 SM x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"}
+                              "sm_count": sms, "sm_mhz": sm_mhz,
+                              "peak_basis": (f"{sms} SMs (queried from the device) x {FP32_LANES_PER_SM} FP32 lanes x "
+                                             f"2 flop x {sm_mhz:.0f} MHz ({clk_src})")}
         # the adjoint (value and query gradient under the same random stream)
         g_out = torch.empty(nq, dtype=torch.float32, device=dev)
         g_grad = torch.empty((nq, 3), dtype=torch.float32, device=dev)
@@ -438,6 +486,22 @@ def run_ours(args):
         result["adjoint"] = {"ms": a0.elapsed_time(a1), "queries_per_s": nq / (a0.elapsed_time(a1) / 1e3)}
         if not args.no_equal_error:
             result["equal_error"] = equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev)
+            summary = {"ordered": {"queries": wl.name,
+                                   "speedup_vs_bh_at_equal_median_error":
+                                       result["equal_error"]["speedup_vs_bh_at_equal_median_error"]}}
+            if args.workload == "winding":
+                # the same sources with as many queries drawn uniformly in their bounding box, unsorted
+                from paper_2506_02219_gb300 import workloads as W
+                wr = W.winding_ellipsoids_random(seed=W.BASE_SEED + 1 + 1000 * rank)
+                Qr = torch.from_numpy(wr.queries).to(dev)
+                rnd = equal_error_compact(sbh, wl, tree, P, M, N, Qr, S, seed, dev)
+                rnd["queries"] = wr.name
+                result["equal_error_random_order"] = rnd
+                summary["random_order"] = {"queries": wr.name,
+                                           "speedup_vs_bh_at_equal_median_error":
+                                               rnd["speedup_vs_bh_at_equal_median_error"]}
+                del Qr
+            result["equal_error_summary"] = summary
         tree.free()
         if world == 1 and not args.no_cpu_baseline:
             v, cores, desc, _ = oracle_throughput(wl, args.cpu_seconds, S)
@@ -447,6 +511,42 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def equal_error_compact(sbh, wl, tree, P, M, N, Q, S, seed, dev,
+                        thetas=(3.0, 2.0, 1.5, 1.2, 1.0, 0.8, 0.67, 0.5, 0.4)):
+    """The estimator at S against the project's Barnes-Hut on one query set: estimator time and
+    median / mean / p99 relative error (65536 sampled queries against the FP64-accumulated GPU brute
+    force), the Barnes-Hut theta sweep with and without warp voting, and the Barnes-Hut time at the
+    estimator's median error (log-log interpolation, the faster voting mode)."""
+    import torch
+    nq = Q.shape[0]
+    kk = _kernel_kwargs(wl)
+    g = torch.Generator(device="cpu").manual_seed(13)
+    idx = torch.randperm(nq, generator=g)[: min(nq, 65536)].sort().values.to(dev)
+    Qs = Q[idx].contiguous()
+    ref = sbh.sbh_eval_brute(P, M, Qs, normals=N, fp64_accum=True, **kk).cpu().numpy()
+    out = sbh.sbh_eval(tree, Q, samples_per_subdomain=S, seed=seed, **kk)
+    ms = timed_ms(lambda: sbh.sbh_eval(tree, Q, samples_per_subdomain=S, seed=seed, out=out, **kk), dev, 3)
+    rel = rel_error(wl.kernel, out[idx].cpu().numpy(), ref)
+    err = float(np.median(rel))
+    bh_out = torch.empty(nq, dtype=torch.float32, device=dev)
+    sweep = []
+    for vote in (True, False):
+        for theta in thetas:
+            t = timed_ms(lambda: sbh.sbh_eval_bh(tree, Q, theta=theta, warp_vote=vote, out=bh_out, **kk), dev, 2)
+            e = rel_error(wl.kernel, sbh.sbh_eval_bh(tree, Qs, theta=theta, warp_vote=vote, **kk).cpu().numpy(), ref)
+            sweep.append({"theta": theta, "warp_vote": vote, "ms": t, "median_rel_err": float(np.median(e))})
+    best = None
+    for vote in (True, False):
+        pts = [(s["median_rel_err"], s["ms"]) for s in sweep if s["warp_vote"] == vote and s["median_rel_err"] > 0]
+        t_bh, extrap = interp_loglog(err, [p[0] for p in pts], [p[1] for p in pts])
+        if best is None or t_bh < best[0]:
+            best = (t_bh, extrap, vote)
+    return {"S": S, "ms": ms, "median_rel_err": err, "tail": tail_errors(rel), "bh_sweep": sweep,
+            "bh_ms_at_equal_error": best[0], "bh_warp_vote": best[2], "extrapolated": best[1],
+            "speedup_vs_bh_at_equal_median_error": best[0] / ms,
+            "error_reference": "GPU brute force with FP64 tile accumulation on 65536 random queries"}
 
 
 def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
@@ -466,19 +566,7 @@ def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
     tail_s = tail_errors(rel_error(wl.kernel, out[idx].cpu().numpy(), ref))
 
     def timed(fn, reps=3):
-        fn()
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(reps):
-            flush_l2(dev)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record()
-            fn()
-            b.record()
-            b.synchronize()
-            ts.append(a.elapsed_time(b))
-        return float(np.median(ts))
+        return timed_ms(fn, dev, reps)
 
     extra = {}
     for s2 in (2, 3, 4, 8, 16, 32):
@@ -579,34 +667,53 @@ def learned_proposal(sbh, wl, tree, Q, idx, ref, seed, kk, timed, near):
 # ------------------------------------------------------------------------------------------------
 # the reference arm: the CPU oracle as it stands
 # ------------------------------------------------------------------------------------------------
+def oracle_full_step(wl, S: int = 1):
+    """One whole step of the oracle on the host cores: its tree build over all sources and its
+    replay of every query. Returns (seconds, cores)."""
+    import oracle
+    kinds = {"coulomb": oracle.COULOMB, "winding": oracle.WINDING, "smoothdist": oracle.SMOOTHDIST}
+    t0 = time.perf_counter()
+    tree = oracle.Tree(wl.points, wl.weights, wl.normals, leaf_size=wl.leaf_size, d=4)
+    tree.replay(wl.queries, S=S, seed=7, kind=kinds[wl.kernel], softening=wl.softening, alpha=wl.alpha)
+    return time.perf_counter() - t0, oracle.max_threads()
+
+
+REFERENCE_BUDGET_S = 200.0  # the timed steps of the reference arm stop short of this
+
+
 def run_reference(args):
+    """The CPU oracle as it stands, timed on the host cores on the same workload: every timed step
+    is a whole step (tree build over all sources + replay of every query), measured. The first
+    warm-up is a whole step too and sizes the run: if K whole steps would take longer than
+    REFERENCE_BUDGET_S, fewer are timed (and reported as the steps taken); the other warm-ups replay
+    a bounded sample."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
     wl = workload_by_name(args.workload, 0)
-    per_step = max(2.0, 150.0 / max(1, args.steps + args.warmup))
-    for _ in range(args.warmup):
-        oracle_throughput(wl, per_step, args.S)
-    vals, ts = [], []
-    for _ in range(args.steps):
-        v, cores, desc, t_full = oracle_throughput(wl, per_step, args.S)
-        vals.append(v)
-        ts.append(t_full)
-    value = float(np.mean(vals))
-    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
-                      "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-                      "ms_per_step": float(np.mean(ts)) * 1e3, "higher_is_better": True, "scaling": "weak",
-                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": wl.name, "sources": int(wl.points.shape[0]),
-                                 "queries": int(wl.queries.shape[0]), "kernel": wl.kernel,
-                                 "samples_per_subdomain": args.S, "leaf_size": wl.leaf_size,
-                                 "step": "oracle tree build + Algorithm 2 replay (FP64, CPU)"},
-                      "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle",
-                                       "sample": desc},
-                      "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0,
-                              "d2h_bytes_per_step": 0}}), flush=True)
+    t_first, cores = oracle_full_step(wl, args.S)
+    for _ in range(args.warmup - 1):
+        oracle_throughput(wl, 2.0, args.S)
+    steps = int(min(args.steps, max(1, REFERENCE_BUDGET_S // t_first)))
+    ts = [oracle_full_step(wl, args.S)[0] for _ in range(steps)]
+    nq = int(wl.queries.shape[0])
+    value = nq * steps / float(np.sum(ts))
+    desc = (f"whole steps: oracle tree build over all {wl.points.shape[0]} sources + replay of all {nq} queries, "
+            f"{steps} timed (first warm-up step {t_first:.2f} s)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "queries/s",
+            "n_gpus": world, "steps": steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean(ts)) * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "sources": int(wl.points.shape[0]), "queries": nq,
+                       "kernel": wl.kernel, "samples_per_subdomain": args.S, "leaf_size": wl.leaf_size,
+                       "step": "oracle tree build + Algorithm 2 replay of every query (FP64, CPU)"},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": cores, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    if steps != args.steps:
+        line["steps_requested"] = args.steps
+    print(json.dumps(line), flush=True)
 
 
 def batched_sets(rank: int = 0, n_sets: int = 64):
@@ -739,7 +846,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="winding",
-                    choices=["winding", "cube", "slice_coulomb", "slice_smoothdist", "far_coulomb", "batched"])
+                    choices=["winding", "winding_random", "cube", "slice_coulomb", "slice_smoothdist", "far_coulomb",
+                             "batched"])
     ap.add_argument("--S", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-equal-error", action="store_true")

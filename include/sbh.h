@@ -133,12 +133,17 @@ typedef struct {
 SBH_API sbh_status sbh_build(const float* points, const float* weights, const float* normals, int64_t n,
                      int32_t leaf_size, void* stream, sbh_tree** out);
 
+/* Most paths per subdomain any evaluation takes (the sample index is carried in 19 bits of a
+ * task tag): every entry point taking samples_per_subdomain returns SBH_EINVAL beyond it. */
+#define SBH_MAX_SAMPLES_PER_SUBDOMAIN (1 << 19)
+
 /* Stochastic estimate of F at nq queries (Algorithm 2 with Eq. 5-7; Sec. 3.3.1 subdomains are
- * the root's children), S = samples_per_subdomain >= 1 paths per subdomain, random stream
- * Philox4x32-10 keyed by `seed` and counted by (query index, subdomain, sample, depth).
+ * the root's children), S = samples_per_subdomain paths per subdomain, 1 <= S <=
+ * SBH_MAX_SAMPLES_PER_SUBDOMAIN, random stream Philox4x32-10 keyed by `seed` and counted by
+ * (query index, subdomain, sample, depth).
  *   queries device [nq][3]; out device [nq]: the estimate of F (the smooth distance for
  *   SBH_SMOOTHDIST). nq = 0 is a no-op. SBH_EINVAL if the kernel is SBH_WINDING and the tree
- *   has no normals, or if an option is out of range. */
+ *   has no normals, if S is out of range, or if an option is out of range. */
 SBH_API sbh_status sbh_eval(const sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel,
                     int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,
                     float* out, void* stream);
@@ -321,9 +326,10 @@ SBH_API const char* sbh_last_error(void);
  * Scratch lives in one static device array of about 0.8 MB that every GPU loading the library
  * holds until the process exits; all calls share it and it keeps the last call's contents, so
  * calls whose GPU work overlaps (on different streams, or from different threads) race and must
- * be ordered by the caller. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before any stream
- * capture. Enqueued on `stream`, no synchronisation. */
+ * be ordered by the caller. Every call looks up the array's device address in the current
+ * device's context (cudaGetSymbolAddress, no allocation), so the address is never stale after a
+ * device reset; the first call on a device also loads the library's device code there, so make
+ * that first call before any stream capture. Enqueued on `stream`, no synchronisation. */
 #define SBH_NOALLOC_MAX_POINTS 65536
 SBH_API sbh_status sbh_morton_sort_noalloc(const float* points, int64_t n, uint64_t* codes, int32_t* perm,
                                            void* stream);

@@ -22,6 +22,21 @@
 namespace sbh {
 static std::atomic<unsigned long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static std::atomic<int> g_sm_count[64];
+int device_sm_count()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    int n = g_sm_count[dev].load(std::memory_order_relaxed);
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+        (void)cudaGetLastError();
+        n = 1;  // no usable device: the launch that follows reports the error
+    }
+    g_sm_count[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
 }  // namespace sbh
 
 namespace {
@@ -172,7 +187,9 @@ sbh_status sbh_eval(const sbh_tree* tree, const float* queries, int64_t nq, sbh_
     g_err[0] = 0;
     if (!tree || !tree->t4.built) return fail(SBH_EINVAL, "tree is NULL or not built");
     if (nq < 0) return fail(SBH_EINVAL, "nq < 0");
-    if (samples_per_subdomain < 1) return fail(SBH_EINVAL, "samples_per_subdomain must be >= 1");
+    if (samples_per_subdomain < 1 || samples_per_subdomain > SBH_MAX_SAMPLES_PER_SUBDOMAIN)
+        return fail(SBH_EINVAL, "samples_per_subdomain = %d outside [1, %d]", (int)samples_per_subdomain,
+                    (int)SBH_MAX_SAMPLES_PER_SUBDOMAIN);
     sbh::KernelParams kp;
     sbh_status st = check_kernel(kernel, &kp);
     if (st != SBH_OK) return st;
@@ -224,7 +241,9 @@ sbh_status sbh_solve_host(const float* points, const float* weights, const float
         (nq > 0 && (device_ptr(queries) || device_ptr(out))))
         return fail(SBH_EINVAL, "sbh_solve_host takes host buffers (use sbh_build and sbh_eval for device ones)");
     if (nq < 0 || chunk < 0) return fail(SBH_EINVAL, "nq and chunk must be >= 0");
-    if (samples_per_subdomain < 1) return fail(SBH_EINVAL, "samples_per_subdomain must be >= 1");
+    if (samples_per_subdomain < 1 || samples_per_subdomain > SBH_MAX_SAMPLES_PER_SUBDOMAIN)
+        return fail(SBH_EINVAL, "samples_per_subdomain = %d outside [1, %d]", (int)samples_per_subdomain,
+                    (int)SBH_MAX_SAMPLES_PER_SUBDOMAIN);
     if (n < 1 || n > kMaxPoints) return fail(SBH_EINVAL, "n = %lld outside [1, 2^28]", (long long)n);
     sbh::KernelParams kp;
     sbh_status st = check_kernel(kernel, &kp);
@@ -236,7 +255,7 @@ sbh_status sbh_solve_host(const float* points, const float* weights, const float
     // each chunk adds a launch tail (~0.15 ms), but the first chunk's evaluation starts after half
     // of the query upload (which outlasts the build where the host link is slow) and its download
     // overlaps the second chunk: two chunks from 2^22 queries on (measured even where the link is
-    // fast: 29.20 ms for one or two chunks at 2^24 queries)
+    // fast: 28.80 ms for one or two chunks at 2^24 queries)
     if (chunk == 0) chunk = nq >= (int64_t(1) << 22) ? (nq + 1) / 2 : std::max<int64_t>(nq, 1);
     // whole 32-query tiles: a tile's results depend on its queries only, so the chunks' tiles must
     // be those of one launch over all queries
@@ -308,7 +327,9 @@ sbh_status sbh_eval_count(const sbh_tree* tree, const float* queries, int64_t nq
     g_err[0] = 0;
     if (!tree || !tree->t4.built) return fail(SBH_EINVAL, "tree is NULL or not built");
     if (nq < 0) return fail(SBH_EINVAL, "nq < 0");
-    if (samples_per_subdomain < 1) return fail(SBH_EINVAL, "samples_per_subdomain must be >= 1");
+    if (samples_per_subdomain < 1 || samples_per_subdomain > SBH_MAX_SAMPLES_PER_SUBDOMAIN)
+        return fail(SBH_EINVAL, "samples_per_subdomain = %d outside [1, %d]", (int)samples_per_subdomain,
+                    (int)SBH_MAX_SAMPLES_PER_SUBDOMAIN);
     sbh::KernelParams kp;
     sbh_status st = check_kernel(kernel, &kp);
     if (st != SBH_OK) return st;
@@ -334,7 +355,9 @@ sbh_status sbh_eval_grad(const sbh_tree* tree, const float* queries, int64_t nq,
     g_err[0] = 0;
     if (!tree || !tree->t4.built) return fail(SBH_EINVAL, "tree is NULL or not built");
     if (nq < 0) return fail(SBH_EINVAL, "nq < 0");
-    if (samples_per_subdomain < 1) return fail(SBH_EINVAL, "samples_per_subdomain must be >= 1");
+    if (samples_per_subdomain < 1 || samples_per_subdomain > SBH_MAX_SAMPLES_PER_SUBDOMAIN)
+        return fail(SBH_EINVAL, "samples_per_subdomain = %d outside [1, %d]", (int)samples_per_subdomain,
+                    (int)SBH_MAX_SAMPLES_PER_SUBDOMAIN);
     sbh::KernelParams kp;
     sbh_status st = check_kernel(kernel, &kp);
     if (st != SBH_OK) return st;
@@ -377,7 +400,9 @@ sbh_status sbh_multi_plan_create(const sbh_tree* const* trees, const float* cons
     if (!plan) return fail(SBH_EINVAL, "plan is NULL");
     *plan = nullptr;
     if (n_sets < 1 || !trees || !queries || !nq || !outs) return fail(SBH_EINVAL, "n_sets >= 1 and non-NULL arrays");
-    if (samples_per_subdomain < 1) return fail(SBH_EINVAL, "samples_per_subdomain must be >= 1");
+    if (samples_per_subdomain < 1 || samples_per_subdomain > SBH_MAX_SAMPLES_PER_SUBDOMAIN)
+        return fail(SBH_EINVAL, "samples_per_subdomain = %d outside [1, %d]", (int)samples_per_subdomain,
+                    (int)SBH_MAX_SAMPLES_PER_SUBDOMAIN);
     sbh::KernelParams kp;
     sbh_status st = check_kernel(kernel, &kp);
     if (st != SBH_OK) return st;
@@ -702,7 +727,9 @@ sbh_status sbh_eval_learned(const sbh_tree* tree, const sbh_mlp* net, const floa
     g_err[0] = 0;
     if (!tree || !tree->t4.built || !net) return fail(SBH_EINVAL, "tree or net missing");
     if (nq < 0) return fail(SBH_EINVAL, "nq < 0");
-    if (samples_per_subdomain < 1) return fail(SBH_EINVAL, "samples_per_subdomain must be >= 1");
+    if (samples_per_subdomain < 1 || samples_per_subdomain > SBH_MAX_SAMPLES_PER_SUBDOMAIN)
+        return fail(SBH_EINVAL, "samples_per_subdomain = %d outside [1, %d]", (int)samples_per_subdomain,
+                    (int)SBH_MAX_SAMPLES_PER_SUBDOMAIN);
     if (!(near >= 0.0f)) return fail(SBH_EINVAL, "near must be >= 0");
     sbh::KernelParams kp;
     sbh_status st = check_kernel(kernel, &kp);

@@ -9,14 +9,14 @@
 // this library's static device memory.
 //
 // The scratch array is a file-scope __device__ array; every GPU that loads the library holds it
-// until the process exits. Host code cannot use the array's name as a device address, so the
-// first call on each device looks up its address with cudaGetSymbolAddress (with that device
-// current) and caches it.
+// until the process exits. Host code cannot use the array's name as a device address, so every
+// call looks up its address with cudaGetSymbolAddress in the current device's context (a lookup,
+// no allocation). The address is not cached: it belongs to the context it was taken in, and a
+// cudaDeviceReset or another context on the same device would leave a cached one stale. The first
+// call on a device also loads this module's device code there.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
-
-#include <mutex>
 
 #include "sbh.h"
 #include "sbh_build.cuh"
@@ -44,9 +44,6 @@ constexpr size_t kScratchBytes = kOffCtrl + round256(2 * sizeof(TreeCtrl));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex g_mu;
-unsigned char* g_scratch_addr[64];
-
 }  // namespace
 
 }  // namespace sbh
@@ -66,26 +63,13 @@ sbh_status sbh_morton_sort_noalloc(const float* points, int64_t n, uint64_t* cod
         set_error_message("sbh_morton_sort_noalloc: points, codes and perm must be non-NULL");
         return SBH_EINVAL;
     }
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess || dev < 0 || dev >= 64) {
-        set_error_message("sbh_morton_sort_noalloc: no usable current device");
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+        set_error_message("sbh_morton_sort_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
         return SBH_ECUDA;
     }
-    unsigned char* base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_addr[dev]) {
-            void* p = nullptr;
-            e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess) {
-                set_error_message("sbh_morton_sort_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-                return SBH_ECUDA;
-            }
-            g_scratch_addr[dev] = (unsigned char*)p;
-        }
-        base = g_scratch_addr[dev];
-    }
+    unsigned char* base = (unsigned char*)p;
     cudaStream_t s = (cudaStream_t)stream;
     uint64_t* keys_tmp = (uint64_t*)(base + kOffKeys);
     int32_t* vals_tmp = (int32_t*)(base + kOffVals);

@@ -232,6 +232,17 @@ def winding_ellipsoids(n_sources: int = 1 << 20, grid: int = 256, seed: int = BA
     return Workload(f"winding_8ellipsoids_{n_sources}src_{grid}cube", p, w, nv, q, "winding")
 
 
+def winding_ellipsoids_random(n_sources: int = 1 << 20, n_queries: int = 1 << 24,
+                              seed: int = BASE_SEED + 1) -> Workload:
+    """The sources of winding_ellipsoids with as many queries drawn uniformly at random in their
+    bounding box, in the order drawn (no spatial coherence between neighbouring queries: the
+    random query sets of the paper's Fig. 4)."""
+    p, w, nv = shape_union(n_sources, seed, n_ellipsoids=8, n_boxes=0)
+    lo, hi = bounding_box(p)
+    q = uniform_box(n_queries, lo, hi, seed + 11)
+    return Workload(f"winding_8ellipsoids_{n_sources}src_{n_queries}random", p, w, nv, q, "winding")
+
+
 def slice_plane_shapes(n_sources: int = 1 << 22, res: int = 1000, kernel: str = "smoothdist",
                        seed: int = BASE_SEED + 2, shuffle: bool = True) -> Workload:
     """Samples on a union of 8 random ellipsoids and 4 boxes, queries on a res x res slice plane

@@ -43,6 +43,36 @@ def rel_error(kind, gpu, ref, alpha=200.0):
     return np.abs(gpu - ref) / np.abs(ref)
 
 
+def plain_rel_error(gpu, ref):
+    """The benchmark spec's tolerance in its stated form: |F_gpu - F_oracle| / |F_oracle| (inf where the
+    oracle's estimate is 0)."""
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(ref != 0.0, np.abs(gpu - ref) / np.abs(ref), np.where(gpu == ref, 0.0, np.inf))
+
+
+def far_from_sources(otree, q):
+    """Mask of the queries farther from every source point than the diagonal of that point's own
+    leaf cell (the cell of its one-point node in the oracle's 64-ary tree). Next to a source the
+    winding kernel's d.N cancels and an FP32 evaluation cannot hold a relative bound. Sources are
+    grouped by the level of their cell, and each group is searched for its nearest point."""
+    from scipy.spatial import cKDTree
+    e = otree.export()
+    m = otree.meta()
+    pts = otree.points.astype(np.float64)
+    leafpt = (e["nchild"] == 0) & (e["end"] - e["begin"] == 1)
+    level = np.full(pts.shape[0], -1)
+    level[e["perm"][e["begin"][leafpt]]] = e["level"][leafpt]
+    qd = np.asarray(q, np.float64)
+    ok = np.ones(qd.shape[0], bool)
+    for lv in np.unique(level):
+        diag = np.inf if lv < 0 else m["diam0"] * np.ldexp(1.0, -2 * int(lv))
+        dist, _ = cKDTree(pts[level == lv]).query(qd, k=1)
+        ok &= dist > diag
+    return ok
+
+
 def oracle_kwargs(oracle_mod, kind, softening=1e-3, alpha=200.0):
     return dict(kind=KIND_ID[kind], softening=softening, alpha=alpha, affine=AFFINE_G)
 

@@ -65,3 +65,12 @@ def test_every_hashed_profile_matches_the_kernel_sources():
         first = open(path).readline().strip()
         assert first.startswith("<!-- source_hash="), path
         assert first == f"<!-- source_hash={want} -->", path
+
+
+def test_fp32_peak_from_sm_count_and_clock():
+    import bench
+    # 152 SMs x 128 lanes x 2 flop x 2070 MHz
+    assert abs(bench.fp32_peak_tflops(152, 2070.0) - 80.54784) < 1e-9
+    assert bench.peak_clock_mhz({"sm_max_mhz": 1965.0})[0] == 1965.0
+    mhz, src = bench.peak_clock_mhz(None)
+    assert mhz > 0 and src

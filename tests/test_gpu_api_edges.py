@@ -33,6 +33,26 @@ def test_solve_host_rejects_bad_arguments(sbh):
         sbh.sbh_solve_host(p, w, q, samples_per_subdomain=0)
 
 
+def test_sample_count_beyond_the_tag_width_is_rejected(sbh):
+    # the warp-task schedule carries the sample index in 19 bits: S = 2^19 is the largest accepted,
+    # beyond it every entry point returns SBH_EINVAL before any launch
+    p, w, q = _cloud(200, 8)
+    t = sbh.sbh_build(dev(p), dev(w))
+    Q = dev(q)
+    big = (1 << 19) + 1
+    with pytest.raises(sbh.SBHError, match="SBH_EINVAL"):
+        sbh.sbh_eval(t, Q, samples_per_subdomain=big)
+    with pytest.raises(sbh.SBHError, match="SBH_EINVAL"):
+        sbh.sbh_eval_grad(t, Q, samples_per_subdomain=big)
+    with pytest.raises(sbh.SBHError, match="SBH_EINVAL"):
+        sbh.sbh_eval_count(t, Q, samples_per_subdomain=big)
+    with pytest.raises(sbh.SBHError, match="SBH_EINVAL"):
+        sbh.sbh_solve_host(p, w, q, samples_per_subdomain=big)
+    with pytest.raises(sbh.SBHError, match="SBH_EINVAL"):
+        sbh.sbh_multi_plan_create([t], [Q], "coulomb", big)
+    assert sbh.sbh_eval(t, Q[:1], samples_per_subdomain=1).shape == (1,)
+
+
 def test_brute_grad_empty_sources_and_queries(sbh):
     import torch
     p, w, q = _cloud(0, 4)

@@ -3,7 +3,11 @@
 - sbh_eval vs the oracle's replay of Algorithm 2 with the same Philox stream: per-query
   estimates within 1e-4 relative to the magnitude of their terms (|F_gpu - F_oracle| <= 1e-4 A,
   A = sum of |terms| >= |F|) on at least 99.9% of queries. Decisions are FP32 on both sides, so
-  nearly every query follows the same paths.
+  nearly every query follows the same paths. Where it is attainable in FP32 the tolerance is also
+  asserted in its plain form, 1e-4 relative to the oracle's estimate on at least 99.9% of queries:
+  for Coulomb everywhere (A / |F| stays below ~11), and for winding numbers at queries farther
+  from every source than that source's leaf cell, relative to max(|F|, 1) as the winding error is
+  defined throughout (outside a closed surface F is near 0).
 - seed-averaged GPU estimates within 3 sigma of the exact sum, sigma from the oracle's
   enumerated variance.
 - sbh_eval_bh without warp voting vs the oracle's Algorithm 1 (identical FP32 far-field
@@ -13,7 +17,7 @@
 import numpy as np
 import pytest
 
-from gpu_util import dev, gpu_kwargs, oracle_kwargs, parity_error, rel_error
+from gpu_util import dev, far_from_sources, gpu_kwargs, oracle_kwargs, parity_error, plain_rel_error, rel_error
 
 pytestmark = pytest.mark.gpu
 
@@ -46,9 +50,18 @@ def test_estimator_matches_replay(sbh, oracle_mod, kind, S, leaf):
     seed = 0x5BA7 + S
     g = sbh.sbh_eval(t, dev(q), samples_per_subdomain=S, seed=seed, **gpu_kwargs(kind)).cpu().numpy()
     kw = oracle_kwargs(oracle_mod, kind)
-    o, A = oracle_mod.Tree(pts, w, nrm, leaf_size=leaf, d=4).replay(q, S=S, seed=seed, return_abs_sum=True, **kw)
+    ot = oracle_mod.Tree(pts, w, nrm, leaf_size=leaf, d=4)
+    o, A = ot.replay(q, S=S, seed=seed, return_abs_sum=True, **kw)
     err = parity_error(kind, g, o, A)
     assert np.mean(err <= TOL) >= 0.999, (np.sort(err)[-10:], np.mean(err <= TOL))
+    if kind == "coulomb":
+        plain = plain_rel_error(g, o)
+        assert np.mean(plain <= TOL) >= 0.999, (np.sort(plain)[-10:], np.mean(plain <= TOL))
+    if kind == "winding":
+        far = far_from_sources(ot, q)
+        assert far.mean() > 0.3
+        plain = np.abs(g[far] - o[far]) / np.maximum(np.abs(o[far]), 1.0)
+        assert np.mean(plain <= TOL) >= 0.999, (np.sort(plain)[-10:], np.mean(plain <= TOL))
 
 
 @pytest.mark.parametrize("sampling,rr,coherent", [(1, 0, 0), (0, 1, 0), (0, 2, 0), (0, 0, 1), (1, 2, 1)])
@@ -62,6 +75,7 @@ def test_estimator_options_match_replay(sbh, oracle_mod, sampling, rr, coherent)
                                           return_abs_sum=True)
     err = parity_error("coulomb", g, r, A)
     assert np.mean(err <= TOL) >= 0.999
+    assert np.mean(plain_rel_error(g, r) <= TOL) >= 0.999
 
 
 @pytest.mark.parametrize("kind", ["coulomb", "winding", "smoothdist"])

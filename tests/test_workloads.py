@@ -43,3 +43,14 @@ def test_far_field_queries_lie_outside_the_sources():
     assert wl.kernel == "coulomb" and wl.points.shape == (5000, 3)
     assert np.all(np.abs(wl.queries).max(1) > 1.2) and np.all(np.abs(wl.queries) <= 3.0)
     assert np.all(np.abs(wl.points) <= 1.0)
+
+
+def test_random_order_winding_queries_share_the_grid_workloads_sources():
+    a = W.winding_ellipsoids(n_sources=4096, grid=8)
+    b = W.winding_ellipsoids_random(n_sources=4096, n_queries=5000)
+    assert np.array_equal(a.points, b.points) and np.array_equal(a.weights, b.weights)
+    lo, hi = a.points.min(0), a.points.max(0)
+    assert b.queries.shape == (5000, 3) and np.all(b.queries >= lo) and np.all(b.queries <= hi)
+    # unsorted: consecutive queries are as far apart as independent uniform draws
+    step = np.linalg.norm(np.diff(b.queries, axis=0), axis=1).mean()
+    assert step > 0.3 * np.linalg.norm(hi - lo)

@@ -24,10 +24,14 @@ def _noalloc(sbh, pts_np):
     P = dev(pts_np)
     codes = torch.empty(n, dtype=torch.int64, device="cuda")
     perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    held, torch_held = sbh.sbh_memory_in_use(), torch.cuda.memory_allocated()
     st = fn(ctypes.c_void_p(P.data_ptr()), n, ctypes.c_void_p(codes.data_ptr()), ctypes.c_void_p(perm.data_ptr()),
             ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 0, sbh.sbh_last_error()
     torch.cuda.synchronize()
+    # the call took no memory from the library's allocator nor from torch's
+    assert sbh.sbh_memory_in_use() == held and torch.cuda.memory_allocated() == torch_held
     return codes.cpu().numpy().view(np.uint64), perm.cpu().numpy()
 
 
