@@ -54,9 +54,10 @@ def flush_l2(dev):
 # FP32 floating-point operations of one kernel term as written in the CUDA kernels (an FMA counts
 # 2, a multiply, add, rsqrt or exp 1): Coulomb 3 sub + r^2 with eps^2 (3 FMA) + rsqrt + scale +
 # accumulate; winding 3 sub + r^2 (2 FMA + mul) + rsqrt + r^-3 (2 mul) + (p - q).N (2 FMA + mul) +
-# 2 mul + accumulate; smooth distance 3 sub + r^2 (2 FMA + mul) + r (rsqrt, mul) + compare +
-# alpha (d - ref) (sub, mul) + exp + FMA; affine 3 sub + g.(p - q) (2 FMA + mul) + add + mul + add.
-FLOPS_PER_TERM = {"coulomb": 12, "winding": 19, "smoothdist": 16, "affine": 11}
+# mul + accumulate (the 1/(4 pi) is applied once per swap); smooth distance 3 sub + r^2 (2 FMA +
+# mul) + r (rsqrt, mul) + compare + alpha (d - ref) (sub, mul) + exp + FMA; affine 3 sub +
+# g.(p - q) (2 FMA + mul) + add + mul + add.
+FLOPS_PER_TERM = {"coulomb": 12, "winding": 18, "smoothdist": 16, "affine": 11}
 # FP32 lanes per SM of a Blackwell SM (two flops per lane per cycle with an FMA); the SM count is
 # read from the device and the clock from the samples taken during the timed region
 FP32_LANES_PER_SM = 128
@@ -484,6 +485,18 @@ def run_ours(args):
         a1.record(stream)
         a1.synchronize()
         result["adjoint"] = {"ms": a0.elapsed_time(a1), "queries_per_s": nq / (a0.elapsed_time(a1) / 1e3)}
+        if args.learned_near is not None:
+            # the learned child proposal alone at one gate: trained, then timed at S = 1 (no error sweep)
+            net = sbh.sbh_mlp_create(1)
+            lo, hi = wl.points.min(0), wl.points.max(0)
+            qt = np.random.default_rng(5).uniform(lo - 0.05 * (hi - lo), hi + 0.05 * (hi - lo),
+                                                  (1024, 3)).astype(np.float32)
+            sbh.sbh_mlp_train(net, tree, torch.from_numpy(qt).to(dev), near=args.learned_near, steps=300, lr=3e-3,
+                              **kk)
+            lout = sbh.sbh_eval_learned(tree, net, Q, seed=seed, near=args.learned_near, **kk)
+            lms = timed_ms(lambda: sbh.sbh_eval_learned(tree, net, Q, seed=seed, near=args.learned_near, out=lout,
+                                                        **kk), dev, 3)
+            result["learned"] = {"near": args.learned_near, "ms": lms, "queries_per_s": nq / (lms / 1e3)}
         if not args.no_equal_error:
             result["equal_error"] = equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev)
             summary = {"ordered": {"queries": wl.name,
@@ -852,6 +865,8 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-equal-error", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--learned-near", type=float, default=None,
+                    help="also train the learned proposal and time it alone at this gate (cell diagonals)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

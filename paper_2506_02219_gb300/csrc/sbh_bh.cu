@@ -87,7 +87,8 @@ cudaError_t launch_bh_eval(const TreeView& T, const float* Q, int64_t nq, const 
 {
     if (nq <= 0) return cudaSuccess;
     int64_t blocks = (nq + 255) / 256;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    const int64_t cap = (int64_t)device_sm_count() * 64;
+    if (blocks > cap) blocks = cap;
     switch (kp.kind) {
     case SBH_COULOMB: launch_bh_kind<SBH_COULOMB>(T, Q, nq, kp, beta, warp_vote, out, s, (unsigned)blocks); break;
     case SBH_WINDING: launch_bh_kind<SBH_WINDING>(T, Q, nq, kp, beta, warp_vote, out, s, (unsigned)blocks); break;

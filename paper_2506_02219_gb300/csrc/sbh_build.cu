@@ -28,8 +28,10 @@ namespace sbh {
 
 namespace {
 constexpr int kThreads = 256;
-inline unsigned grid_for(int64_t n, int per_block = kThreads, unsigned cap = 152u * 16u)
+// blocks for n items, at most 16 per SM of the current device (grid-stride loops do the rest)
+inline unsigned grid_for(int64_t n, int per_block = kThreads, unsigned cap = 0)
 {
+    if (cap == 0) cap = 16u * (unsigned)device_sm_count();
     int64_t g = (n + per_block - 1) / per_block;
     if (g < 1) g = 1;
     return (unsigned)(g > cap ? cap : g);

@@ -234,7 +234,8 @@ cudaError_t launch_lane_impl(const TreeView& T, const float* Q, int64_t nq, cons
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     const int threads = 256;
     int64_t blocks = (nq + threads - 1) / threads;
-    if (blocks > 152 * SBH_LANE_GRID_BLOCKS_PER_SM) blocks = 152 * SBH_LANE_GRID_BLOCKS_PER_SM;
+    const int64_t cap = (int64_t)device_sm_count() * SBH_LANE_GRID_BLOCKS_PER_SM;
+    if (blocks > cap) blocks = cap;
     const unsigned b = (unsigned)blocks;
     switch (kp.kind) {
     case SBH_COULOMB:

@@ -2,13 +2,16 @@
 // Algorithm 2) organised for full SIMT lanes.
 //
 // The arithmetic and the random stream are those of Algorithm 2 (see sbh_eval.cu for the
-// statement); what differs is how a warp schedules the work of its 32 queries. Per subdomain a
-// every lane takes the depth-0 decision of its own query (same node, so the child records and
-// prefix fractions it reads are the same addresses for all lanes). Everything after that is a task:
+// statement); what differs is how a warp schedules the work of its 32 queries. Every decision is
+// a task:
 //   decision task  (query, node T, depth k, ...): draw the child, play the roulette (Eq. 5);
 //   swap task      (query, node T, weight w):     add w * Delta_T (Eq. 6) to the query's sum.
-// A continuing decision emits one swap task and one decision task for the chosen child. Tasks
-// wait in two per-warp rings in shared memory and are run 32 at a time, one per lane, so the
+// A continuing decision emits one swap task and, unless the child is a source point, one
+// decision task for the chosen child. The random block of a decision is drawn when its task is
+// made (at depth 0 per subdomain, every lane for its own query): a draw whose roulette stops the
+// path whichever child is picked (certain_stop) makes no task at all, so the pick, the child's
+// record and the roulette test run only for paths that may continue. Tasks wait in two per-warp
+// rings in shared memory and are run 32 at a time, one per lane, so the
 // lanes stay busy however the paths of the 32 queries diverge. Swap results reach a query's sum
 // through a lane-ordered reduction among the tasks of that query, so results are deterministic.
 //
@@ -34,6 +37,27 @@ namespace {
 #ifndef SBH_STAGE_MAX
 #define SBH_STAGE_MAX 128
 #endif
+// a subdomain's depth-0 decisions are taken in place by the warp when more than this many of its
+// lanes may continue, else queued as decision tasks
+// A subdomain's depth-0 decisions are taken in place by the warp (every lane at the same node)
+// when more than this many of its lanes may continue, else queued as decision tasks. Measured on
+// the estimator: 24. The adjoint and learned instances always queue them (32): their larger code
+// ran slower with the decision inlined twice, and queueing let the learned one keep its state in
+// registers.
+#ifndef SBH_DEPTH0_QUEUE_MAX
+#define SBH_DEPTH0_QUEUE_MAX 24
+#endif
+// resident blocks per SM of the adjoint instance: 3 (80 registers) measured 7% faster than 4
+#ifndef SBH_GRAD_MIN_BLOCKS
+#define SBH_GRAD_MIN_BLOCKS 3
+#endif
+template <bool LEARNED, bool GRAD>
+constexpr int depth0_queue_max() { return (LEARNED || GRAD) ? 32 : SBH_DEPTH0_QUEUE_MAX; }
+// resident blocks per SM of the learned-proposal instance (its per-warp scoring scratch takes
+// shared memory: three blocks fit)
+#ifndef SBH_LEARNED_MIN_BLOCKS
+#define SBH_LEARNED_MIN_BLOCKS 3
+#endif
 // most blocks launched per SM (the rest of the tiles are taken in grid-stride order)
 #ifndef SBH_GRID_BLOCKS_PER_SM
 #define SBH_GRID_BLOCKS_PER_SM 96
@@ -55,6 +79,8 @@ constexpr int swap_unroll() { return KIND == SBH_WINDING ? SBH_SWAP_UNROLL_WINDI
 struct WarpState {
     // decision tasks
     int32_t d_node[kRing];
+    uint32_t d_x0[kRing];    // the decision's random words: child pick
+    uint32_t d_x1[kRing];    //                              roulette
     uint32_t d_tag[kRing];   // slot | depth << 5 | sample << 13
     int32_t d_ai[kRing];
     float d_prr[kRing];
@@ -70,6 +96,7 @@ struct WarpState {
     uint32_t qctr[32];       // counter word 0 of each query's random stream
     float acc[32];           // sum of the swap terms (smooth distance: in units of exp(-alpha ref))
     float ref[32];
+    float slack;             // certain_stop's slack for the current tree
 };
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
@@ -80,35 +107,44 @@ __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << lane_id()) - 1
 // shared memory at start and reads them there; everything else is read through L1.
 constexpr int kStageMax = SBH_STAGE_MAX;
 
+// The stage sits at the start of the dynamic shared memory in a fixed layout of kStageMax entries
+// per array, so that its arrays are constant shared-memory addresses (no pointers held in
+// registers): pm [kStageMax] float4, dip [kStageMax] float4 (winding kernel only), cdf, meta and
+// fc [kStageMax] 4-byte words. What else a block keeps in dynamic shared memory follows it.
+extern __shared__ float4 s_dyn[];
+constexpr size_t kStageBytes = (size_t)kStageMax * (2 * sizeof(float4) + 3 * sizeof(uint32_t));
+static_assert(kStageBytes % 16 == 0, "the region after the stage stays 16-byte aligned");
+
 struct Stage {
     int32_t lo;       // first staged node id
-    uint32_t n;       // number of staged nodes
-    float4* pm;
-    float4* dip;      // winding kernel only
-    float* cdf;
-    uint32_t* meta;
-    int32_t* fc;
+    uint32_t n;       // number of staged nodes (0: nothing staged)
+    __device__ __forceinline__ static float4* pm() { return s_dyn; }
+    __device__ __forceinline__ static float4* dip() { return s_dyn + kStageMax; }
+    __device__ __forceinline__ static float* cdf() { return reinterpret_cast<float*>(s_dyn + 2 * kStageMax); }
+    __device__ __forceinline__ static uint32_t* meta() { return reinterpret_cast<uint32_t*>(cdf() + kStageMax); }
+    __device__ __forceinline__ static int32_t* fc() { return reinterpret_cast<int32_t*>(meta() + kStageMax); }
+    __device__ __forceinline__ static unsigned char* after() { return reinterpret_cast<unsigned char*>(s_dyn) + kStageBytes; }
 };
 
 __device__ __forceinline__ float4 ld_pm(const TreeView& T, const Stage& S, int32_t v)
 {
     const uint32_t i = (uint32_t)(v - S.lo);
-    return i < S.n ? S.pm[i] : __ldg(&T.pm[v]);
+    return i < S.n ? Stage::pm()[i] : __ldg(&T.pm[v]);
 }
 __device__ __forceinline__ float4 ld_dip(const TreeView& T, const Stage& S, int32_t v)
 {
     const uint32_t i = (uint32_t)(v - S.lo);
-    return i < S.n ? S.dip[i] : __ldg(&T.dip[v]);
+    return i < S.n ? Stage::dip()[i] : __ldg(&T.dip[v]);
 }
 __device__ __forceinline__ uint32_t ld_meta(const TreeView& T, const Stage& S, int32_t v)
 {
     const uint32_t i = (uint32_t)(v - S.lo);
-    return i < S.n ? S.meta[i] : __ldg(&T.meta[v]);
+    return i < S.n ? Stage::meta()[i] : __ldg(&T.meta[v]);
 }
 __device__ __forceinline__ int32_t ld_fc(const TreeView& T, const Stage& S, int32_t v)
 {
     const uint32_t i = (uint32_t)(v - S.lo);
-    return i < S.n ? S.fc[i] : __ldg(&T.fc[v]);
+    return i < S.n ? Stage::fc()[i] : __ldg(&T.fc[v]);
 }
 
 // m f(p, q) of a node record (not used for the smooth distance, which works in exp frames)
@@ -131,7 +167,7 @@ __device__ __forceinline__ int pick_child(const TreeView& T, const Stage& S, int
     if (sampling == 0) {
         const float u = unit24(x);
         const bool st = f >= S.lo && (uint32_t)(f + nc - S.lo) <= S.n;
-        const float* cdf = st ? S.cdf + (f - S.lo) : T.cdf + f;
+        const float* cdf = st ? Stage::cdf() + (f - S.lo) : T.cdf + f;
         int lo = 0, hi = nc - 1;
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
@@ -154,7 +190,12 @@ __device__ __forceinline__ int pick_child(const TreeView& T, const Stage& S, int
 
 // per-warp scratch of the learned pick: one chunk of FP16 feature rows, the rows of one group of
 // decisions (exp of the clamped score, child mass), and the gated decisions of the batch
-constexpr int kLearnRows = 256;
+// (rows per group of decisions: 128 keeps three blocks' shared memory within an SM's)
+#ifndef SBH_LEARN_ROWS
+#define SBH_LEARN_ROWS 128
+#endif
+constexpr int kLearnRows = SBH_LEARN_ROWS;
+static_assert(kLearnRows >= 64 && kLearnRows <= 256, "a group holds at least one decision's 64 children; rk is 8-bit");
 struct __align__(16) LearnScratch {
     uint32_t A[32 * kChunkWords];
     float sc[32];
@@ -178,6 +219,7 @@ struct Params {
     KernelParams kp;
     int S;
     uint2 key;
+    PhiloxRoundKeys rk;      // the round keys of key
     int sampling, rr, coherent, raw_sum;
     float* out;
     int64_t qbase;           // index of the first query in the caller's whole query set (chunked runs)
@@ -227,8 +269,6 @@ __device__ __forceinline__ void learned_picks(const Params& P, const Stage& S, c
         L.lndT[k] = __logf((t2 > 0.0f ? t2 * rsqrtf(t2) : 0.0f) + 1e-6f * BT);
     }
     const int G = __popc(gm);
-    MlpRegs Wr;
-    load_mlp_regs(*P.frag, Wr);
     __syncwarp();
     for (int base_k = 0; base_k < G;) {
         const int off_base = L.off[base_k];
@@ -276,7 +316,7 @@ __device__ __forceinline__ void learned_picks(const Params& P, const Stage& S, c
             }
             store_feature_row(&L.A[lane * kChunkWords], x, live);
             __syncwarp();
-            const float sco = score_chunk(Wr, L.A, L.sc);
+            const float sco = score_chunk_shared(*P.frag, L.A, L.sc);
             // segmented inclusive prefix sums over the lanes, restarting at each decision's head
             float pe = live ? __expf(clamp_score(sco)) : 0.0f, pm = mc;
             const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
@@ -319,13 +359,27 @@ __device__ __forceinline__ void learned_picks(const Params& P, const Stage& S, c
     }
 }
 
-// One decision per lane (Algorithm 2's loop body up to the break test). On a continue the lane
-// appends a swap task for its node and a decision task for the chosen child.
+// The random block of the decision (query slot, subdomain ai, sample, depth) of a path now at a
+// node at distance dT with cell diagonal BT; false when its roulette stops the path whichever child
+// is picked (certain_stop), which then needs no decision task.
+__device__ __forceinline__ bool draw_decision(const Params& P, const WarpState& W, uint32_t slot, int32_t ai,
+                                              uint32_t sample, uint32_t depth, float dT, float BT, uint32_t& x0,
+                                              uint32_t& x1)
+{
+    const uint4 x = philox4x32_10(make_uint4(W.qctr[slot], (uint32_t)ai, sample, depth), P.rk);
+    x0 = x.x;
+    x1 = x.y;
+    return !certain_stop(P.rr, unit24(x.y), dT, BT, W.slack);
+}
+
+// One decision per lane (Algorithm 2's loop body up to the break test), its random words x0, x1
+// drawn when the task was made. On a continue the lane appends a swap task for its node and, if
+// the chosen child's own decision may continue, a decision task for the child.
 // With the learned proposal, wT carries p(path reaches node) (the product of the picks'
 // probabilities) and wa = 1, so that p_agg = wT / wa in both cases.
 template <int KIND, bool LEARNED>
 __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpState& W, const float* sdiam, bool valid,
-                                       int32_t node,
+                                       int32_t node, uint32_t x0, uint32_t x1,
                                        uint32_t tag, int32_t ai, float prr, float dT, float wT, float wa,
                                        uint32_t& d_tail, uint32_t& s_tail)
 {
@@ -336,13 +390,12 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
     const uint32_t slot = tag & 31u;
     const uint32_t depth = (tag >> 5) & 0xFFu;
     float3 q = make_float3(0.0f, 0.0f, 0.0f);
-    uint4 x = make_uint4(0u, 0u, 0u, 0u);
     uint32_t mT = 0;
     int32_t f = 0;
     int nc = 0;
+    uint32_t y0 = 0, y1 = 0;  // the child's decision, drawn on a continue
     if (valid) {
         q = make_float3(W.qx[slot], W.qy[slot], W.qz[slot]);
-        x = philox4x32_10(make_uint4(W.qctr[slot], (uint32_t)ai, tag >> 13, depth), P.key);
         mT = ld_meta(T, S, node);
         f = ld_fc(T, S, node);
         nc = (int)meta_nchild(mT);
@@ -354,12 +407,12 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
         const bool gated = valid && learned_gate(nc, dT, P.near, BT);
         const unsigned gm = __ballot_sync(0xFFFFFFFFu, gated);
         if (valid && !gated) {
-            child = f + pick_child(T, S, node, f, nc, x.x, 0);
+            child = f + pick_child(T, S, node, f, nc, x0, 0);
             pick_prob = -pT.w;  // a mass pick: its probability m_c / m_T is formed on a continue
         }
-        if (gm) learned_picks<KIND>(P, S, sdiam, gm, gated, q, pT, BT, f, nc, unit24(x.x), child, pick_prob);
+        if (gm) learned_picks<KIND>(P, S, sdiam, gm, gated, q, pT, BT, f, nc, unit24(x0), child, pick_prob);
     } else {
-        if (valid) child = f + pick_child(T, S, node, f, nc, x.x, P.sampling);
+        if (valid) child = f + pick_child(T, S, node, f, nc, x0, P.sampling);
     }
     if (valid) {
         const float4 pc = ld_pm(T, S, child);
@@ -367,15 +420,18 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
         dc = dist_rn(pc.x, pc.y, pc.z, q);
         float p = 1.0f;
         const uint32_t lT = meta_level(mT);
-        cont = rr_continue(P.rr, unit24(x.y), dT, sdiam[lT], lT, dc, meta_level(mc), p);
+        cont = rr_continue(P.rr, unit24(x1), dT, sdiam[lT], lT, dc, meta_level(mc), p);
         if (cont) {
             prr2 = prr * p;
             w = __fdiv_rn(wa, wT * prr2 * (float)P.S);  // 1 / (p_agg p_rr S), p_agg = wT / wa
             if constexpr (LEARNED) wc = wT * (pick_prob < 0.0f ? pc.w / -pick_prob : pick_prob);
             else wc = P.sampling ? (float)(__ldg(&T.ne[child]) - __ldg(&T.nb[child])) : pc.w;
             // a path that reaches a source point stops there: no decision task for it (levels
-            // strictly increase, so depth < kMaxDepth always holds; the test only guards a damaged tree)
-            if (meta_kind(mc) == kPoint || depth + 1 >= (uint32_t)kMaxDepth) wc = -1.0f;
+            // strictly increase, so depth < kMaxDepth always holds; the test only guards a damaged
+            // tree); nor does one whose next roulette stops it whichever child it draws
+            if (meta_kind(mc) == kPoint || depth + 1 >= (uint32_t)kMaxDepth ||
+                !draw_decision(P, W, slot, ai, tag >> 13, depth + 1, dc, sdiam[meta_level(mc)], y0, y1))
+                wc = -1.0f;
         }
     }
     const unsigned push_s = __ballot_sync(0xFFFFFFFFu, cont);
@@ -388,6 +444,8 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
         if (wc >= 0.0f) {
             const uint32_t k = (d_tail + __popc(push_d & lanemask_lt())) & kRingMask;
             W.d_node[k] = child;
+            W.d_x0[k] = y0;
+            W.d_x1[k] = y1;
             W.d_tag[k] = tag + (1u << 5);  // depth + 1
             W.d_ai[k] = ai;
             W.d_prr[k] = prr2;
@@ -411,16 +469,16 @@ __device__ __forceinline__ void decision_batch(const Params& P, const Stage& S, 
     const uint32_t take = avail < 32u ? avail : 32u;
     const bool valid = lane_id() < take;
     int32_t node = 0, ai = 0;
-    uint32_t tag = 0;
+    uint32_t tag = 0, x0 = 0, x1 = 0;
     float prr = 0.f, dT = 0.f, wT = 0.f, wa = 1.f;
     if (valid) {
         const uint32_t i = (d_head + lane_id()) & kRingMask;
         node = W.d_node[i]; tag = W.d_tag[i]; ai = W.d_ai[i]; prr = W.d_prr[i]; dT = W.d_dT[i];
-        wT = W.d_wT[i]; wa = W.d_wa[i];
+        wT = W.d_wT[i]; wa = W.d_wa[i]; x0 = W.d_x0[i]; x1 = W.d_x1[i];
     }
     __syncwarp();  // every task is read before new ones may reuse its slot
     d_head += take;
-    decide<KIND, LEARNED>(P, S, W, sdiam, valid, node, tag, ai, prr, dT, wT, wa, d_tail, s_tail);
+    decide<KIND, LEARNED>(P, S, W, sdiam, valid, node, x0, x1, tag, ai, prr, dT, wT, wa, d_tail, s_tail);
 }
 
 // m f(p, q) and its gradient in q (added to g), for the adjoint: the kernel ∇_q f applied to the
@@ -452,6 +510,24 @@ __device__ __forceinline__ float term_vg(float4 pm, float4 dp, float3 q, const K
     }
 }
 
+// The winding term and its query gradient times 4 pi (sums of them are scaled by 1 / (4 pi) once):
+// value (d.N) / r^3, gradient -N / r^3 + 3 (d.N) d / r^5 (added to g); 0 at r = 0
+__device__ __forceinline__ float winding_vg_4pi(float4 pm, float4 dp, float3 q, float g[3])
+{
+    const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    if (!(r2 > 0.0f)) return 0.0f;
+    const float ir = rsqrtf(r2);
+    const float ir2 = ir * ir;
+    const float ir3 = ir2 * ir;
+    const float t = fmaf(dx, dp.x, fmaf(dy, dp.y, dz * dp.z)) * ir3;  // (d.N) / r^3
+    const float c = 3.0f * t * ir2;                                   // 3 (d.N) / r^5
+    g[0] = fmaf(c, dx, fmaf(-ir3, dp.x, g[0]));
+    g[1] = fmaf(c, dy, fmaf(-ir3, dp.y, g[1]));
+    g[2] = fmaf(c, dz, fmaf(-ir3, dp.z, g[2]));
+    return t;
+}
+
 // smooth distance: add m exp(-alpha (d - ref)) and its gradient to (v, g) in the frame exp(-alpha ref),
 // lowering ref to d first when d is smaller (v and g scale together)
 __device__ __forceinline__ void smooth_vg(float4 pm, float3 q, float alpha, float wm, float& ref, float& v, float g[3])
@@ -473,13 +549,115 @@ __device__ __forceinline__ void smooth_vg(float4 pm, float3 q, float alpha, floa
     }
 }
 
-// Run up to 32 swap tasks: w * (sum_children m_c f(p_c, q) - m_T f(p_T, q)), added to the
-// query's sum in lane order. GRAD: the same for the terms' query gradients.
+// One swap: w * (sum_children m_c f(p_c, q) - m_T f(p_T, q)) at node `node` for the query at q.
+// v gets the value (smooth distance: in the frame exp(-alpha r), r the smallest distance met);
+// GRAD: g gets the same for the terms' query gradients.
+template <int KIND, bool GRAD>
+__device__ __forceinline__ void swap_terms(const Params& P, const Stage& S, int32_t node, float3 q, float w, float& v,
+                                           float& r, float g[3])
+{
+    const TreeView& T = P.T;
+    const uint32_t m = ld_meta(T, S, node);
+    const int32_t f = ld_fc(T, S, node);
+    const int nc = (int)meta_nchild(m);
+    const float4 pT = ld_pm(T, S, node);
+    // the children are read through one pointer: all staged (a subdomain's children) or all
+    // from global memory (a node whose children straddle the end of the stage reads them there)
+    const bool st = f >= S.lo && (uint32_t)(f + nc - S.lo) <= S.n;
+    const float4* cp = st ? Stage::pm() + (f - S.lo) : T.pm + f;
+    if constexpr (GRAD && KIND == SBH_SMOOTHDIST) {
+        const float a = P.kp.alpha;
+        smooth_vg(pT, q, a, -w * pT.w, r, v, g);
+        for (int k = 0; k < nc; ++k) smooth_vg(cp[k], q, a, w * cp[k].w, r, v, g);
+    } else if constexpr (GRAD && KIND == SBH_WINDING) {
+        const float4* cd = st ? Stage::dip() + (f - S.lo) : T.dip + f;
+        float s0 = 0.0f;
+        for (int k = 0; k < nc; ++k) s0 += winding_vg_4pi(cp[k], cd[k], q, g);
+        float go[3] = {0.0f, 0.0f, 0.0f};
+        const float own = winding_vg_4pi(pT, ld_dip(T, S, node), q, go);
+        const float ws = w * kInv4Pi;
+        v = ws * (s0 - own);
+        g[0] = ws * (g[0] - go[0]); g[1] = ws * (g[1] - go[1]); g[2] = ws * (g[2] - go[2]);
+    } else if constexpr (GRAD) {
+        float s0 = 0.0f;
+        for (int k = 0; k < nc; ++k) s0 += term_vg<KIND>(cp[k], cp[k], q, P.kp, g);
+        float go[3] = {0.0f, 0.0f, 0.0f};
+        const float own = term_vg<KIND>(pT, pT, q, P.kp, go);
+        v = w * (s0 - own);
+        g[0] = w * (g[0] - go[0]); g[1] = w * (g[1] - go[1]); g[2] = w * (g[2] - go[2]);
+    } else if constexpr (KIND == SBH_SMOOTHDIST) {
+        const float a = P.kp.alpha;
+        r = dist_fast(pT, q);
+        v = -w * pT.w;
+        for (int k = 0; k < nc; ++k) {
+            const float4 pc = cp[k];
+            const float d = dist_fast(pc, q);
+            if (d < r) { v *= __expf(-a * (r - d)); r = d; }
+            v = fmaf(w * pc.w, __expf(-a * (d - r)), v);
+        }
+    } else {
+        // two independent partial sums: two child records in flight per iteration
+        const float4* cd = KIND == SBH_WINDING ? (st ? Stage::dip() + (f - S.lo) : T.dip + f) : cp;
+        float s0 = 0.0f, s1 = 0.0f;
+        int k = 0;
+        constexpr int kUnroll = swap_unroll<KIND>();
+#pragma unroll kUnroll
+        for (; k + 1 < nc; k += 2) {
+            const float4 p0 = cp[k], p1 = cp[k + 1];
+            if constexpr (KIND == SBH_WINDING) {
+                const float4 d0 = cd[k], d1 = cd[k + 1];
+                s0 += term_winding_4pi(p0, d0, q);
+                s1 += term_winding_4pi(p1, d1, q);
+            } else {
+                s0 += node_value<KIND>(T, S, f + k, p0, q, P.kp);
+                s1 += node_value<KIND>(T, S, f + k + 1, p1, q, P.kp);
+            }
+        }
+        if (k < nc) {
+            if constexpr (KIND == SBH_WINDING) s0 += term_winding_4pi(cp[k], cd[k], q);
+            else s0 += node_value<KIND>(T, S, f + k, cp[k], q, P.kp);
+        }
+        if constexpr (KIND == SBH_WINDING)
+            v = (w * kInv4Pi) * ((s0 + s1) - term_winding_4pi(pT, ld_dip(T, S, node), q));
+        else
+            v = w * ((s0 + s1) - node_value<KIND>(T, S, node, pT, q, P.kp));
+    }
+}
+
+// Add a query's summed swap results (value tot in the frame exp(-alpha tr) for the smooth
+// distance; GRAD: gradient tg) into its sums in shared memory.
+template <int KIND, bool GRAD>
+__device__ __forceinline__ void add_to_query(const Params& P, WarpState& W, uint32_t slot, float tot, float tr,
+                                             const float tg[3])
+{
+    float* qg = GRAD ? P.gsum + (threadIdx.x >> 5) * 96 + 3 * slot : nullptr;
+    if constexpr (KIND == SBH_SMOOTHDIST) {
+        const float a = P.kp.alpha;
+        float qr = W.ref[slot], qa = W.acc[slot];
+        if (tr < qr) {
+            const float f = __expf(-a * (qr - tr));
+            qa = qa * f + tot;
+            if (GRAD) for (int c = 0; c < 3; ++c) qg[c] = qg[c] * f + tg[c];
+            qr = tr;
+        } else {
+            const float f = __expf(-a * (tr - qr));
+            qa = fmaf(tot, f, qa);
+            if (GRAD) for (int c = 0; c < 3; ++c) qg[c] = fmaf(tg[c], f, qg[c]);
+        }
+        W.ref[slot] = qr;
+        W.acc[slot] = qa;
+    } else {
+        W.acc[slot] += tot;
+        if (GRAD) for (int c = 0; c < 3; ++c) qg[c] += tg[c];
+    }
+}
+
+// Run up to 32 swap tasks from the front of the ring, one per lane, each added to its query's sum
+// in lane order.
 template <int KIND, bool GRAD>
 __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, WarpState& W, uint32_t& s_head,
                                            uint32_t s_tail)
 {
-    const TreeView& T = P.T;
     const uint32_t avail = s_tail - s_head;
     const uint32_t take = avail < 32u ? avail : 32u;
     const bool valid = lane_id() < take;
@@ -496,64 +674,7 @@ __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, Warp
     s_head += take;
     float v = 0.0f, r = 3.0e38f;
     float g[3] = {0.0f, 0.0f, 0.0f};
-    if (valid) {
-        const float3 q = make_float3(W.qx[slot], W.qy[slot], W.qz[slot]);
-        const uint32_t m = ld_meta(T, S, node);
-        const int32_t f = ld_fc(T, S, node);
-        const int nc = (int)meta_nchild(m);
-        const float4 pT = ld_pm(T, S, node);
-        // the children are read through one pointer: all staged (a subdomain's children) or all
-        // from global memory (a node whose children straddle the end of the stage reads them there)
-        const bool st = f >= S.lo && (uint32_t)(f + nc - S.lo) <= S.n;
-        const float4* cp = st ? S.pm + (f - S.lo) : T.pm + f;
-        if constexpr (GRAD && KIND == SBH_SMOOTHDIST) {
-            const float a = P.kp.alpha;
-            smooth_vg(pT, q, a, -w * pT.w, r, v, g);
-            for (int k = 0; k < nc; ++k) smooth_vg(cp[k], q, a, w * cp[k].w, r, v, g);
-        } else if constexpr (GRAD) {
-            const float4* cd = KIND == SBH_WINDING ? (st ? S.dip + (f - S.lo) : T.dip + f) : cp;
-            float s0 = 0.0f;
-            for (int k = 0; k < nc; ++k) s0 += term_vg<KIND>(cp[k], cd[k], q, P.kp, g);
-            float go[3] = {0.0f, 0.0f, 0.0f};
-            const float4 dT = KIND == SBH_WINDING ? ld_dip(T, S, node) : pT;
-            const float own = term_vg<KIND>(pT, dT, q, P.kp, go);
-            v = w * (s0 - own);
-            g[0] = w * (g[0] - go[0]); g[1] = w * (g[1] - go[1]); g[2] = w * (g[2] - go[2]);
-        } else if constexpr (KIND == SBH_SMOOTHDIST) {
-            const float a = P.kp.alpha;
-            r = dist_fast(pT, q);
-            v = -w * pT.w;
-            for (int k = 0; k < nc; ++k) {
-                const float4 pc = cp[k];
-                const float d = dist_fast(pc, q);
-                if (d < r) { v *= __expf(-a * (r - d)); r = d; }
-                v = fmaf(w * pc.w, __expf(-a * (d - r)), v);
-            }
-        } else {
-            // two independent partial sums: two child records in flight per iteration
-            const float4* cd = KIND == SBH_WINDING ? (st ? S.dip + (f - S.lo) : T.dip + f) : cp;
-            float s0 = 0.0f, s1 = 0.0f;
-            int k = 0;
-            constexpr int kUnroll = swap_unroll<KIND>();
-#pragma unroll kUnroll
-            for (; k + 1 < nc; k += 2) {
-                const float4 p0 = cp[k], p1 = cp[k + 1];
-                if constexpr (KIND == SBH_WINDING) {
-                    const float4 d0 = cd[k], d1 = cd[k + 1];
-                    s0 += term_winding(p0, d0, q);
-                    s1 += term_winding(p1, d1, q);
-                } else {
-                    s0 += node_value<KIND>(T, S, f + k, p0, q, P.kp);
-                    s1 += node_value<KIND>(T, S, f + k + 1, p1, q, P.kp);
-                }
-            }
-            if (k < nc) {
-                if constexpr (KIND == SBH_WINDING) s0 += term_winding(cp[k], cd[k], q);
-                else s0 += node_value<KIND>(T, S, f + k, cp[k], q, P.kp);
-            }
-            v = w * ((s0 + s1) - node_value<KIND>(T, S, node, pT, q, P.kp));
-        }
-    }
+    if (valid) swap_terms<KIND, GRAD>(P, S, node, make_float3(W.qx[slot], W.qy[slot], W.qz[slot]), w, v, r, g);
     // lane-ordered sum over the tasks of each query
     const unsigned peers = __match_any_sync(0xFFFFFFFFu, slot);
     float tot = 0.0f, tr = 3.0e38f;
@@ -584,28 +705,7 @@ __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, Warp
             if (GRAD) for (int c = 0; c < 3; ++c) tg[c] += gs[c];
         }
     }
-    if (valid && lane_id() == (uint32_t)(__ffs(peers) - 1)) {
-        float* qg = GRAD ? P.gsum + (threadIdx.x >> 5) * 96 + 3 * slot : nullptr;
-        if constexpr (KIND == SBH_SMOOTHDIST) {
-            const float a = P.kp.alpha;
-            float qr = W.ref[slot], qa = W.acc[slot];
-            if (tr < qr) {
-                const float f = __expf(-a * (qr - tr));
-                qa = qa * f + tot;
-                if (GRAD) for (int c = 0; c < 3; ++c) qg[c] = qg[c] * f + tg[c];
-                qr = tr;
-            } else {
-                const float f = __expf(-a * (tr - qr));
-                qa = fmaf(tot, f, qa);
-                if (GRAD) for (int c = 0; c < 3; ++c) qg[c] = fmaf(tg[c], f, qg[c]);
-            }
-            W.ref[slot] = qr;
-            W.acc[slot] = qa;
-        } else {
-            W.acc[slot] += tot;
-            if (GRAD) for (int c = 0; c < 3; ++c) qg[c] += tg[c];
-        }
-    }
+    if (valid && lane_id() == (uint32_t)(__ffs(peers) - 1)) add_to_query<KIND, GRAD>(P, W, slot, tot, tr, tg);
     __syncwarp();
 }
 
@@ -627,6 +727,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
     W.qctr[lane] = P.coherent ? 0u : (uint32_t)(j + P.qbase);
     W.acc[lane] = 0.0f;
     W.ref[lane] = 3.0e38f;
+    if (lane == 0) W.slack = stop_slack(T.ctrl->lo, T.ctrl->side, sdiam[0]);
     float* qg = GRAD ? P.gsum + (threadIdx.x >> 5) * 96 + 3 * lane : nullptr;
     if (GRAD) { qg[0] = 0.0f; qg[1] = 0.0f; qg[2] = 0.0f; }
     __syncwarp();
@@ -656,10 +757,35 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
         if (meta_kind(ma) == kPoint) continue;
         const float wa = LEARNED ? 1.0f : (P.sampling ? (float)(__ldg(&T.ne[a]) - __ldg(&T.nb[a])) : pa.w);
         const float da = dist_rn(pa.x, pa.y, pa.z, q);
+        const float Ba = sdiam[meta_level(ma)];
         for (int s = 0; s < P.S; ++s) {
-            decide<KIND, LEARNED>(P, S, W, sdiam, active, a, lane | ((uint32_t)s << 13), ai, 1.0f, da, wa, wa, d_tail,
-                                  s_tail);
-            while (s_tail - s_head >= 32u) swap_batch<KIND, GRAD>(P, S, W, s_head, s_tail);
+            // the depth-0 decision of every lane's query, unless its roulette surely stops: taken in
+            // place by the whole warp (the node is the same for every lane) when enough lanes need it,
+            // else queued as tasks that a later batch runs with other work
+            uint32_t x0 = 0, x1 = 0;
+            const bool live = active && draw_decision(P, W, lane, ai, (uint32_t)s, 0u, da, Ba, x0, x1);
+            const unsigned push = __ballot_sync(0xFFFFFFFFu, live);
+            constexpr int kQueueMax = depth0_queue_max<LEARNED, GRAD>();
+            if (kQueueMax < 0 || (kQueueMax < 32 && __popc(push) > kQueueMax)) {
+                decide<KIND, LEARNED>(P, S, W, sdiam, live, a, x0, x1, lane | ((uint32_t)s << 13), ai, 1.0f, da, wa, wa,
+                                      d_tail, s_tail);
+                while (s_tail - s_head >= 32u) swap_batch<KIND, GRAD>(P, S, W, s_head, s_tail);
+            } else {
+                if (live) {
+                    const uint32_t k = (d_tail + __popc(push & lanemask_lt())) & kRingMask;
+                    W.d_node[k] = a;
+                    W.d_x0[k] = x0;
+                    W.d_x1[k] = x1;
+                    W.d_tag[k] = lane | ((uint32_t)s << 13);
+                    W.d_ai[k] = ai;
+                    W.d_prr[k] = 1.0f;
+                    W.d_dT[k] = da;
+                    W.d_wT[k] = wa;
+                    W.d_wa[k] = wa;
+                }
+                d_tail += __popc(push);
+                __syncwarp();
+            }
             while (d_tail - d_head >= 32u) {
                 decision_batch<KIND, LEARNED>(P, S, W, sdiam, d_head, d_tail, s_tail);
                 while (s_tail - s_head >= 32u) swap_batch<KIND, GRAD>(P, S, W, s_head, s_tail);
@@ -709,8 +835,8 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
     __syncwarp();
 }
 
-// dynamic shared memory: [learned proposal: MlpFrag, one LearnScratch per warp | adjoint: one
-// [32][3] gradient sum per warp] then the stage
+// dynamic shared memory: the stage (kStageBytes), then [learned proposal: MlpFrag, one LearnScratch
+// per warp | adjoint: one [32][3] gradient sum per warp]
 template <bool LEARNED, bool GRAD>
 constexpr size_t extra_smem_bytes()
 {
@@ -719,38 +845,30 @@ constexpr size_t extra_smem_bytes()
 }
 
 template <int KIND, bool LEARNED, bool GRAD>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, LEARNED ? 2 : SBH_BATCHED_MIN_BLOCKS)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock,
+                                  LEARNED ? SBH_LEARNED_MIN_BLOCKS : (GRAD ? SBH_GRAD_MIN_BLOCKS : SBH_BATCHED_MIN_BLOCKS))
     k_stoch_batched(Params P, int32_t stage_lo, uint32_t stage_n)
 {
     __shared__ WarpState s_state[kWarpsPerBlock];
     __shared__ float sdiam[LEARNED ? 2 * kDiamLevels : kDiamLevels];  // learned: then ln of each
-    extern __shared__ float4 s_dyn[];
-    float4* s_stage = s_dyn;
     if constexpr (LEARNED) {
-        MlpFrag* F = reinterpret_cast<MlpFrag*>(s_dyn);
+        MlpFrag* F = reinterpret_cast<MlpFrag*>(Stage::after());
         mlp_frag_fill(P.mlpw, *F);
         P.frag = F;
-        P.learn = reinterpret_cast<LearnScratch*>(reinterpret_cast<unsigned char*>(s_dyn) + sizeof(MlpFrag));
-        s_stage = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_dyn) + extra_smem_bytes<LEARNED, GRAD>());
+        P.learn = reinterpret_cast<LearnScratch*>(Stage::after() + sizeof(MlpFrag));
     } else if constexpr (GRAD) {
-        P.gsum = reinterpret_cast<float*>(s_dyn);
-        s_stage = reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_dyn) + extra_smem_bytes<LEARNED, GRAD>());
+        P.gsum = reinterpret_cast<float*>(Stage::after());
     }
     Stage S;
     S.lo = stage_lo;
     S.n = stage_n;
-    S.pm = s_stage;
-    S.dip = s_stage + stage_n;
-    S.cdf = (float*)(S.dip + (KIND == SBH_WINDING ? stage_n : 0));
-    S.meta = (uint32_t*)(S.cdf + stage_n);
-    S.fc = (int32_t*)(S.meta + stage_n);
     for (uint32_t i = threadIdx.x; i < stage_n; i += blockDim.x) {
         const int32_t v = stage_lo + (int32_t)i;
-        S.pm[i] = __ldg(&P.T.pm[v]);
-        if (KIND == SBH_WINDING) S.dip[i] = __ldg(&P.T.dip[v]);
-        S.cdf[i] = __ldg(&P.T.cdf[v]);
-        S.meta[i] = __ldg(&P.T.meta[v]);
-        S.fc[i] = __ldg(&P.T.fc[v]);
+        Stage::pm()[i] = __ldg(&P.T.pm[v]);
+        if (KIND == SBH_WINDING) Stage::dip()[i] = __ldg(&P.T.dip[v]);
+        Stage::cdf()[i] = __ldg(&P.T.cdf[v]);
+        Stage::meta()[i] = __ldg(&P.T.meta[v]);
+        Stage::fc()[i] = __ldg(&P.T.fc[v]);
     }
     if (threadIdx.x < kDiamLevels) {
         sdiam[threadIdx.x] = P.T.ctrl->diam[threadIdx.x];
@@ -797,8 +915,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, SBH_BATCHED_MIN_BLOCKS) k
     WarpState& W = s_state[warp];
     float* sdiam = s_diam[warp];
     Params& P = s_params[warp];
-    Stage S;
-    S.lo = 0; S.n = 0; S.pm = nullptr; S.dip = nullptr; S.cdf = nullptr; S.meta = nullptr; S.fc = nullptr;
+    Stage S;  // nothing staged: the sets' trees differ
+    S.lo = 0; S.n = 0;
     const uint32_t lane = lane_id();
     if (lane == 0) P = M.base;
     __syncwarp();
@@ -829,8 +947,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, SBH_BATCHED_MIN_BLOCKS) k
 template <int KIND, bool LEARNED, bool GRAD>
 static cudaError_t launch_kind(const Params& P, unsigned blocks, int32_t lo, uint32_t n, cudaStream_t s)
 {
-    const size_t bytes = extra_smem_bytes<LEARNED, GRAD>() +
-                         (size_t)n * (sizeof(float4) * (KIND == SBH_WINDING ? 2 : 1) + 3 * sizeof(uint32_t));
+    const size_t bytes = kStageBytes + extra_smem_bytes<LEARNED, GRAD>();
     cudaError_t e = cudaFuncSetAttribute(k_stoch_batched<KIND, LEARNED, GRAD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -851,11 +968,13 @@ static cudaError_t launch_batched_impl(const TreeView& T, const TreeCtrl& host_c
     P.gsum = nullptr;
     P.T = T; P.Q = Q; P.nq = nq; P.kp = kp; P.S = S;
     P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    P.rk = philox_round_keys(P.key);
     P.sampling = o.sampling; P.rr = o.rr; P.coherent = o.seed_mode; P.raw_sum = o.raw_sum; P.out = out;
     P.mlpw = (const __half*)mlp_half; P.near = near; P.frag = nullptr; P.learn = nullptr;
     const int64_t tiles = (nq + 31) / 32;
     int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    if (blocks > 152 * SBH_GRID_BLOCKS_PER_SM) blocks = 152 * SBH_GRID_BLOCKS_PER_SM;
+    const int64_t grid_cap = (int64_t)device_sm_count() * SBH_GRID_BLOCKS_PER_SM;
+    if (blocks > grid_cap) blocks = grid_cap;
     // stage the first nodes of generations 1 and 2 (the subdomains, then their children), at most
     // kStageMax (half as many with the learned proposal, whose scratch takes room)
     const int32_t lo = host_ctrl.max_depth >= 1 ? host_ctrl.depth_base[1] : 0;
@@ -913,11 +1032,12 @@ cudaError_t launch_stoch_multi(const void* set_descs, int n_sets, int64_t total_
     P.grad = nullptr; P.gsum = nullptr;
     P.mlpw = nullptr; P.near = 0.0f; P.frag = nullptr; P.learn = nullptr;
     P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    P.rk = philox_round_keys(P.key);
     P.sampling = o.sampling; P.rr = o.rr; P.coherent = o.seed_mode; P.raw_sum = o.raw_sum;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     // persistent: as many blocks as are resident at once
-    const unsigned blocks = 152 * SBH_BATCHED_MIN_BLOCKS;
+    const unsigned blocks = (unsigned)device_sm_count() * SBH_BATCHED_MIN_BLOCKS;
     switch (kp.kind) {
     case SBH_COULOMB: k_stoch_multi<SBH_COULOMB><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(M); break;
     case SBH_WINDING: k_stoch_multi<SBH_WINDING><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(M); break;

@@ -14,6 +14,9 @@ namespace sbh {
 
 // host-side count of kernel launches made by the library (reported by sbh_kernel_launches)
 void note_launch();
+// streaming multiprocessors of the current device (queried once per device, then cached); grid
+// caps and persistent launches are sized in multiples of it
+int device_sm_count();
 // set the calling thread's sbh_last_error() message (printf-style)
 void set_error_message(const char* fmt, ...);
 
@@ -77,6 +80,33 @@ struct TreeView {
 // the halves and xors in the other words and the key; the key advances by the Weyl increments
 // between rounds.
 // ----------------------------------------------------------------------------------------------
+// The ten round keys of a key (k.x + r W0, k.y + r W1 for round r), precomputed once per launch
+// so that a round's key words are read as operands instead of advanced in registers.
+struct PhiloxRoundKeys {
+    uint32_t k[20];
+};
+__host__ __device__ inline PhiloxRoundKeys philox_round_keys(uint2 k)
+{
+    PhiloxRoundKeys K;
+    for (int r = 0; r < 10; ++r) {
+        K.k[2 * r] = k.x + (uint32_t)r * 0x9E3779B9u;
+        K.k[2 * r + 1] = k.y + (uint32_t)r * 0xBB67AE85u;
+    }
+    return K;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxRoundKeys& K)
+{
+    constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(kM0, c.x), lo0 = kM0 * c.x;
+        const uint32_t hi1 = __umulhi(kM1, c.z), lo1 = kM1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ K.k[2 * r], lo1, hi0 ^ c.w ^ K.k[2 * r + 1], lo0);
+    }
+    return c;
+}
+
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
 {
     constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
@@ -125,6 +155,39 @@ __device__ __forceinline__ bool rr_continue(int rr, float u, float dT, float BT,
     return true;
 }
 
+// A path at node T (distance dT from the query to T's centre, cell diagonal BT) stops at its next
+// roulette whichever child is drawn when u >= p_c for every child c; this test finds such draws
+// before the child is drawn, so the pick, the child's record and the exact test above are skipped
+// for them. It never skips a path rr_continue would continue, so results do not change.
+//   Every child centre lies in T's cell grown by `slack`: points are assigned to cells by FP32
+//   rounding (at most one quantisation step, side 2^-20, outside their cell per axis) and centres
+//   are rounded to FP32; the caller passes slack = diam0 2^-19 + 2^-20 max |coordinate|. So
+//   d_c >= dT - BT - slack, and X = max(dT, BT) 4^-(l_c - l_T) <= dT / 4 when dT > BT (a child is
+//   at least one level down): p_c = X / d_c <= dT / (4 (dT - BT - slack)). The test asks for
+//   4 u (dT - BT - slack) >= dT (1 + 2^-10); the margin covers the rounding of the FP32
+//   distances (a few units in the last place) many times over. Roulette off never stops; the
+//   fixed 1/2 stops exactly when u >= 1/2.
+__device__ __forceinline__ bool certain_stop(int rr, float u, float dT, float BT, float slack)
+{
+    if (rr == 1) return false;
+    if (rr == 2) return u >= 0.5f;
+    const float g = dT - (BT + slack);
+    return g > 0.0f && 4.0f * u * g >= dT * 1.0009765625f;
+}
+
+// the slack of certain_stop for a tree (its root cube: lower corner lo, edge side, diagonal diam0)
+__host__ __device__ inline float stop_slack(const float lo[3], float side, float diam0)
+{
+    float c = 0.0f;
+    for (int a = 0; a < 3; ++a) {
+        const float x0 = lo[a] < 0.0f ? -lo[a] : lo[a];
+        const float x1 = lo[a] + side < 0.0f ? -(lo[a] + side) : lo[a] + side;
+        c = c > x0 ? c : x0;
+        c = c > x1 ? c : x1;
+    }
+    return diam0 * 1.9073486328125e-06f + c * 9.5367431640625e-07f;  // 2^-19, 2^-20
+}
+
 // ----------------------------------------------------------------------------------------------
 // Kernel terms m f(p, q) in FP32 (values; tolerances, not bit-exactness, apply to these).
 // ----------------------------------------------------------------------------------------------
@@ -153,6 +216,17 @@ __device__ __forceinline__ float term_winding(float4 pm, float4 dp, float3 q)
     const float ir = rsqrtf(r2);
     const float dot = fmaf(dx, dp.x, fmaf(dy, dp.y, dz * dp.z));
     const float v = dot * (ir * ir * ir) * kInv4Pi;
+    return r2 > 0.0f ? v : 0.0f;
+}
+
+// The winding term times 4 pi, ((p - q).N) / r^3: sums of these are scaled by 1 / (4 pi) once
+__device__ __forceinline__ float term_winding_4pi(float4 pm, float4 dp, float3 q)
+{
+    const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float ir = rsqrtf(r2);
+    const float dot = fmaf(dx, dp.x, fmaf(dy, dp.y, dz * dp.z));
+    const float v = dot * (ir * ir * ir);
     return r2 > 0.0f ? v : 0.0f;
 }
 

@@ -211,7 +211,6 @@ __global__ void k_dataset(TreeView T, const float4* __restrict__ spw, const floa
 // No atomics: the gradient, and so the whole training, is the same bit for bit on every run.
 // ------------------------------------------------------------------------------------------------
 constexpr int kTrainWarps = 4;
-constexpr int kTrainBlocksMax = 152 * 8;
 constexpr int kPartStride = kMlpParams + 1;  // a block's row: the gradient, then its loss
 
 __global__ void __launch_bounds__(32 * kTrainWarps) k_loss_grad(const float* __restrict__ wg,
@@ -355,7 +354,8 @@ cudaError_t mlp_alloc(MlpState& M, cudaStream_t s)
     if (e == cudaSuccess) e = dalloc((void**)&M.v, kMlpParams * sizeof(float), s);
     if (e == cudaSuccess) e = dalloc((void**)&M.grad, kMlpParams * sizeof(float), s);
     if (e == cudaSuccess) e = dalloc((void**)&M.loss, sizeof(float), s);
-    if (e == cudaSuccess) e = dalloc((void**)&M.part, (size_t)kTrainBlocksMax * kPartStride * sizeof(float), s);
+    M.part_blocks = 8 * device_sm_count();
+    if (e == cudaSuccess) e = dalloc((void**)&M.part, (size_t)M.part_blocks * kPartStride * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(M.m, 0, kMlpParams * sizeof(float), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(M.v, 0, kMlpParams * sizeof(float), s);
     return e;
@@ -379,7 +379,8 @@ cudaError_t mlp_scores(const MlpState& M, const float* feats, int64_t n, float* 
 {
     if (n <= 0) return cudaSuccess;
     int64_t blocks = ((n + 31) / 32 + kScoreWarps - 1) / kScoreWarps;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    const int64_t cap = 8 * (int64_t)device_sm_count();
+    if (blocks > cap) blocks = cap;
     k_scores<<<(unsigned)blocks, 32 * kScoreWarps, 0, s>>>(M.wh, feats, n, out);
     note_launch();
     return cudaGetLastError();
@@ -394,7 +395,7 @@ cudaError_t mlp_loss_grad(MlpState& M, const float* feats, const float* targets,
         return e;
     }
     int64_t blocks = (n_sets + kTrainWarps - 1) / kTrainWarps;
-    if (blocks > kTrainBlocksMax) blocks = kTrainBlocksMax;
+    if (blocks > M.part_blocks) blocks = M.part_blocks;  // the partial sums are then added in a fixed order
     k_loss_grad<<<(unsigned)blocks, 32 * kTrainWarps, 0, s>>>(M.w, feats, targets, off, n_sets, 1.0f / (float)n_sets,
                                                              M.part);
     note_launch();
@@ -441,7 +442,8 @@ cudaError_t mlp_dataset(const sbh_tree* tree, const float* Q, const int32_t* set
     if (n_sets <= 0) return cudaSuccess;
     const TreeView T = tree->t4.view();
     int64_t blocks = (n_sets * 32 + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    const int64_t cap = 16 * (int64_t)device_sm_count();
+    if (blocks > cap) blocks = cap;
     const unsigned b = (unsigned)blocks;
     switch (kp.kind) {
     case SBH_COULOMB: k_dataset<SBH_COULOMB><<<b, 256, 0, s>>>(T, tree->spw, tree->snrm, Q, set_q, set_node, n_sets, set_off, kp, feats, targets); break;

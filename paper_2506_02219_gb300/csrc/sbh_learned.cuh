@@ -282,6 +282,56 @@ __device__ __forceinline__ float score_chunk(const MlpRegs& W, const uint32_t* A
     return r;
 }
 
+// The same scores with the weight operands read from the block's shared-memory fragments at each
+// use instead of held in registers (every lane reads its own word of a fragment: no bank
+// conflicts; the biases and output weights are broadcasts). For kernels whose other state leaves
+// no room for the 41 registers of MlpRegs.
+__device__ __forceinline__ float score_chunk_shared(const MlpFrag& F, const uint32_t* A, float* sc)
+{
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll 1
+    for (int mb = 0; mb < 2; ++mb) {
+        const uint32_t* r0 = A + (mb * 16 + g) * kChunkWords;
+        const uint32_t* r1 = r0 + 8 * kChunkWords;
+        const uint32_t a[4] = {r0[t], r1[t], r0[4 + t], r1[4 + t]};
+        uint32_t a2[2][4];
+#pragma unroll
+        for (int ks = 0; ks < 2; ++ks) {
+            float c0[4] = {0.0f, 0.0f, 0.0f, 0.0f}, c1[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            mma16816(c0, a, F.b1[2 * ks][0][lane], F.b1[2 * ks][1][lane]);
+            mma16816(c1, a, F.b1[2 * ks + 1][0][lane], F.b1[2 * ks + 1][1][lane]);
+            a2[ks][0] = pack_relu_half2(c0[0], c0[1]);
+            a2[ks][1] = pack_relu_half2(c0[2], c0[3]);
+            a2[ks][2] = pack_relu_half2(c1[0], c1[1]);
+            a2[ks][3] = pack_relu_half2(c1[2], c1[3]);
+        }
+        float s_lo = 0.0f, s_hi = 0.0f;  // rows g and g + 8 of the m-block
+#pragma unroll
+        for (int nt = 0; nt < 4; ++nt) {
+            const int n0 = nt * 8 + 2 * t;
+            const float bb0 = F.bias2[n0], bb1 = F.bias2[n0 + 1];
+            float c2[4] = {bb0, bb1, bb0, bb1};
+            mma16816(c2, a2[0], F.b2[0][nt][0][lane], F.b2[0][nt][1][lane]);
+            mma16816(c2, a2[1], F.b2[1][nt][0][lane], F.b2[1][nt][1][lane]);
+            const float w0 = F.w3[n0], w1 = F.w3[n0 + 1];
+            s_lo = fmaf(w0, fmaxf(c2[0], 0.0f), fmaf(w1, fmaxf(c2[1], 0.0f), s_lo));
+            s_hi = fmaf(w0, fmaxf(c2[2], 0.0f), fmaf(w1, fmaxf(c2[3], 0.0f), s_hi));
+        }
+        s_lo += __shfl_xor_sync(0xFFFFFFFFu, s_lo, 1);
+        s_lo += __shfl_xor_sync(0xFFFFFFFFu, s_lo, 2);
+        s_hi += __shfl_xor_sync(0xFFFFFFFFu, s_hi, 1);
+        s_hi += __shfl_xor_sync(0xFFFFFFFFu, s_hi, 2);
+        if (t == 0) {
+            sc[mb * 16 + g] = s_lo + F.b3;
+            sc[mb * 16 + g + 8] = s_hi + F.b3;
+        }
+    }
+    __syncwarp();
+    const float r = sc[lane];
+    __syncwarp();
+    return r;
+}
+
 // device state of one network
 struct MlpState {
     float* w = nullptr;     // FP32 master weights
@@ -291,6 +341,7 @@ struct MlpState {
     float* grad = nullptr;
     float* loss = nullptr;
     float* part = nullptr;  // per-block partial gradients of the last loss evaluation
+    int part_blocks = 0;    // blocks part holds room for (8 per SM of the device it was made on)
     int64_t step = 0;
 };
 
