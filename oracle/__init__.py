@@ -82,6 +82,8 @@ def _load():
         lib.sbho_tree_build_ex.argtypes = [P, P, P, i64, i32, i32, i32, i32, i32]
         lib.sbho_tree_build_ex.restype = P
         lib.sbho_bh_work.argtypes = [P, P, i64, C.c_float, P]
+        lib.sbho_replay_cut.argtypes = [P, C.POINTER(_Kernel), P, i64, C.c_float, u64, P, P]
+        lib.sbho_enumerate_cut.argtypes = [P, C.POINTER(_Kernel), P, i64, C.c_float, P, P]
         lib.sbho_tree_free.argtypes = [P]
         lib.sbho_tree_nnodes.argtypes = [P]
         lib.sbho_tree_nnodes.restype = i64
@@ -334,6 +336,28 @@ class Tree:
         self._lib.sbho_enumerate_learned(self._h, C.byref(k), _ptr(w), C.c_double(eps), C.c_float(near), _ptr(q),
                                          q.shape[0],
                                          _ptr(mean), _ptr(var))
+        return mean, var
+
+    def replay_cut(self, queries, beta_s: float, seed: int = 0, kind=COULOMB, softening=1e-3, alpha=200.0,
+                   affine=(0.0, 0.0, 0.0)):
+        """The estimator with per-query subdomains taken as the Barnes-Hut contribution nodes at beta_s
+        (the alternative cover Sec. 3.3.1 names), S = 1, mass p_agg, Eq. 5 roulette. Returns (estimate,
+        work per query: the walk's far-field tests plus every swap's children and node)."""
+        q = _f32(queries, 3)
+        out = np.zeros(q.shape[0], np.float64)
+        work = np.zeros(q.shape[0], np.int64)
+        k = kernel(kind, softening, alpha, affine)
+        self._lib.sbho_replay_cut(self._h, C.byref(k), _ptr(q), q.shape[0], C.c_float(beta_s),
+                                  C.c_uint64(seed & (2**64 - 1)), _ptr(out), _ptr(work))
+        return out, work
+
+    def enumerate_cut(self, queries, beta_s: float, kind=COULOMB, softening=1e-3, alpha=200.0, affine=(0.0, 0.0, 0.0)):
+        """Exact (mean, variance) of replay_cut's estimator per query, by enumeration."""
+        q = _f32(queries, 3)
+        mean = np.zeros(q.shape[0], np.float64)
+        var = np.zeros(q.shape[0], np.float64)
+        k = kernel(kind, softening, alpha, affine)
+        self._lib.sbho_enumerate_cut(self._h, C.byref(k), _ptr(q), q.shape[0], C.c_float(beta_s), _ptr(mean), _ptr(var))
         return mean, var
 
     def enumerate(self, queries, kind=COULOMB, softening=1e-3, alpha=200.0, affine=(0.0, 0.0, 0.0),

@@ -957,6 +957,63 @@ SBHO_API void sbho_enumerate_grad(const void *h, const sbho_kernel *k, const flo
 }
 
 /* ------------------------------------------------------------------------------------------ */
+/* Subdomains taken per query as the Barnes-Hut contribution nodes at beta_s (Sec. 3.3.1 names  */
+/* this cover as an alternative to the root's children): Algorithm 1's walk with parameter      */
+/* beta_s gives nodes that partition the sources; each one gets its control variate and one path */
+/* of Algorithm 2 started from it (Philox counter (query, index of the node in the walk's order, */
+/* 0, depth)). An oracle-only study of the paper's alternative; the CUDA path does not build it. */
+/* work[j] counts the walk's far-field tests, plus a swap's children and node for every swap.    */
+/* ------------------------------------------------------------------------------------------ */
+static void bh_cut(const otree *t, int64_t v, const float q32[3], float beta, int64_t *out, int64_t *n,
+                   int64_t *tests)
+{
+    ++*tests;
+    if (t->nchild[v] == 0 || ffratio32(t, v, q32) >= beta) { out[(*n)++] = v; return; }
+    for (int c = 0; c < t->nchild[v]; ++c) bh_cut(t, t->first_child[v] + c, q32, beta, out, n, tests);
+}
+
+SBHO_API void sbho_replay_cut(const void *h, const sbho_kernel *k, const float *queries, int64_t nq, float beta_s,
+                              uint64_t seed, double *out, int64_t *work)
+{
+    const otree *t = (const otree *)h;
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+#pragma omp parallel
+    {
+        int64_t *subs = (int64_t *)malloc((size_t)t->n_nodes * sizeof(int64_t));
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t j = 0; j < nq; ++j) {
+            float q32[3] = {queries[3 * j], queries[3 * j + 1], queries[3 * j + 2]};
+            double q[3] = {q32[0], q32[1], q32[2]};
+            int64_t ns = 0, tests = 0;
+            bh_cut(t, 0, q32, beta_s, subs, &ns, &tests);
+            double F = 0;
+            int64_t W = tests;
+            for (int64_t ai = 0; ai < ns; ++ai) {
+                int64_t a = subs[ai], T = a;
+                uint32_t depth = 0;
+                double prr = 1.0;
+                F += node_term(t, k, a, q);
+                while (t->nchild[T] > 0) {
+                    uint32_t ctr[4] = {(uint32_t)j, (uint32_t)ai, 0u, depth}, x[4];
+                    sbho_philox4x32_10(ctr, key, x);
+                    int64_t c = pick_child(t, T, x[0], SAMPLE_MASS);
+                    float p;
+                    if (!rr_continue32(t, T, c, q32, RR_PAPER, unit24f(x[1]), &p)) break;
+                    prr *= (double)p;
+                    F += swap_delta(t, k, T, q) / (p_in(t, T, a, SAMPLE_MASS) * prr);
+                    W += t->nchild[T] + 1;
+                    T = c;
+                    ++depth;
+                }
+            }
+            out[j] = F;
+            if (work) work[j] = W;
+        }
+        free(subs);
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
 /* Learned child proposal (a project extension; the paper samples the path index uniformly and  */
 /* names importance sampling as future work, Sec. 3.3). A 6-32-32-1 ReLU network scores each    */
 /* child c of a node T from query-relative features; the proposal mixes its softmax with the    */
@@ -1210,6 +1267,31 @@ SBHO_API void sbho_enumerate(const void *h, const sbho_kernel *k, const float *q
         mean[j] = E;
         var[j] = Var;
     }
+}
+
+
+/* exact mean and variance of the one-sample estimator with the Barnes-Hut-cut subdomains */
+SBHO_API void sbho_enumerate_cut(const void *h, const sbho_kernel *k, const float *queries, int64_t nq, float beta_s,
+                                 double *mean, double *var)
+{
+    const otree *t = (const otree *)h;
+    int64_t *subs = (int64_t *)malloc((size_t)t->n_nodes * sizeof(int64_t));
+    for (int64_t j = 0; j < nq; ++j) {
+        const float *q32 = &queries[3 * j];
+        double q[3] = {q32[0], q32[1], q32[2]};
+        int64_t ns = 0, tests = 0;
+        bh_cut(t, 0, q32, beta_s, subs, &ns, &tests);
+        double E = 0, Var = 0;
+        for (int64_t ai = 0; ai < ns; ++ai) {
+            moments m = {0, 0};
+            enum_rec(t, k, subs[ai], subs[ai], q, 1.0, 0.0, 1.0, SAMPLE_MASS, RR_PAPER, &m);
+            E += node_term(t, k, subs[ai], q) + m.e1;
+            Var += m.e2 - m.e1 * m.e1;
+        }
+        mean[j] = E;
+        var[j] = Var;
+    }
+    free(subs);
 }
 
 /* thread control for the timed CPU baseline */

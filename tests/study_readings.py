@@ -16,6 +16,9 @@ Run as ``python tests/study_readings.py [--n 32768] [--seeds 8]``. It prints one
   over beta in [0.5, 48] (Sec. 4.2, Fig. 4's rule); bh_work_eq / est_work < 1 means Barnes-Hut
   reaches the same median error with less work.
 
+The last rows take the subdomains per query as the Barnes-Hut contribution nodes at beta_s (the
+cover Sec. 3.3.1 names as future work); their work includes that walk's far-field tests.
+
 This is a measurement script, not a test: it asserts nothing. The oracle is test infrastructure,
 which is why the script lives beside the tests.
 """
@@ -99,6 +102,23 @@ def main():
             eq = bh_work_at(t2, q, F, med)
             print(f"{name} | {qname} | {med:.2e} | {wk:.0f} | {bias:.1e} | {bh2_med:.2e} | {bh2_work:.0f} | "
                   f"{med / bh2_med:.1f} | {eq / wk:.2f}", flush=True)
+    t = O.Tree(P, w)
+    for beta_s in (0.5, 1.0, 1.5, 2.0, 3.0):
+        for qname, q in qs.items():
+            F = Fs[qname]
+            errs, work = [], []
+            for s in range(args.seeds):
+                est, wk = t.replay_cut(q, beta_s, seed=1000 + s)
+                errs.append(np.abs(est - F))
+                work.append(wk.mean())
+            med, wk = float(np.median(np.concatenate(errs))), float(np.mean(work))
+            mean, _ = t.enumerate_cut(q[:256], beta_s)
+            bias = float(np.median(np.abs(mean - F[:256])))
+            bh2_med = float(np.median(np.abs(t2.bh(q, 2.0) - F)))
+            eq = bh_work_at(t2, q, F, med)
+            print(f"cell, subdomains = Barnes-Hut cut at beta_s = {beta_s:g} | {qname} | {med:.2e} | {wk:.0f} | "
+                  f"{bias:.1e} | {bh2_med:.2e} | {float(t2.bh_work(q, 2.0).mean()):.0f} | {med / bh2_med:.1f} | "
+                  f"{eq / wk:.2f}", flush=True)
 
 
 if __name__ == "__main__":

@@ -40,6 +40,9 @@ MUTATIONS = {
     "subdomains one generation too deep": (
         "if (gen[v] == sub_gen || (gen[v] < sub_gen && t->nchild[v] == 0))",
         "if (gen[v] == sub_gen + 1 || (gen[v] < sub_gen + 1 && t->nchild[v] == 0))"),
+    "Barnes-Hut cut without its leaves": (
+        "if (t->nchild[v] == 0 || ffratio32(t, v, q32) >= beta) { out[(*n)++] = v; return; }",
+        "if (t->nchild[v] == 0) return;\n    if (ffratio32(t, v, q32) >= beta) { out[(*n)++] = v; return; }"),
     "Philox key schedule": ("if (round > 0) { k0 += weyl0; k1 += weyl1; }",
                             "if (round > 1) { k0 += weyl0; k1 += weyl1; }"),
     "winding gradient missing its r^-5 term": (

@@ -10,7 +10,9 @@ also build the others, so that what each does to the estimator can be measured:
   p = 0 and the swap above a one-point node is never taken. The estimator is truncated; a hand
   case fixes its mean exactly.
 - single-child chains kept as nodes (their swaps are 0, so the mean is unchanged).
-- subdomains taken g generations below the root (Sec. 3.3.1 allows any cover of the sources).
+- subdomains taken g generations below the root (Sec. 3.3.1 allows any cover of the sources);
+- subdomains taken per query as the Barnes-Hut contribution nodes at beta_s (the cover Sec. 3.3.1
+  names as future work).
 
 The last test keeps the measured finding these options serve: on a Table-1-like case (one
 closed surface rescaled into [-1, 1]^3, masses summing to 1, the Coulomb kernel, grid and random
@@ -158,3 +160,31 @@ def test_estimator_loses_to_barnes_hut_on_a_table1_like_case(oracle_mod):
         t = oracle_mod.Tree(P, wt, **opts)
         e_est = np.median(np.abs(np.concatenate([t.replay(q, seed=s) for s in range(8)]) - np.tile(F, 8)))
         assert e_est > 5.0 * e_bh, (opts, e_est, e_bh)
+
+
+@pytest.mark.parametrize("kind", ["coulomb", "winding", "smoothdist"])
+@pytest.mark.parametrize("beta_s", [0.5, 1.0, 2.0])
+def test_barnes_hut_cut_subdomains_keep_the_theorem(oracle_mod, kind, beta_s):
+    pts, w, normals, q, F, kw = _problem(oracle_mod, 300, 31, kind)
+    t = oracle_mod.Tree(pts, w, normals)
+    mean, var = t.enumerate_cut(q, beta_s, **kw)
+    scale = np.maximum(np.abs(F), 1e-3 if kind == "winding" else 0.0)
+    assert np.all(np.abs(mean - F) <= 1e-12 * scale + 1e-15), (mean - F) / scale
+    assert np.all(var >= -1e-12 * scale * scale)
+
+
+def test_barnes_hut_cut_limits(oracle_mod):
+    pts, w, normals, q, F, kw = _problem(oracle_mod, 200, 8, "coulomb")
+    t = oracle_mod.Tree(pts, w)
+    # beta_s = inf: the cut is every leaf (here every source point), so the estimate is the exact sum
+    est, work = t.replay_cut(q, float("inf"), seed=3)
+    np.testing.assert_allclose(est, F, rtol=1e-13)
+    assert np.all(work == t.n_nodes)  # every node tested once, no swap
+    # beta_s = 0: the root alone is the cut; unbiased, with variance
+    mean, var = t.enumerate_cut(q, 0.0)
+    np.testing.assert_allclose(mean, F, rtol=1e-12)
+    assert np.all(var > 0)
+    # the replay samples that distribution: the mean of many seeds approaches the exact sum
+    est = np.mean([t.replay_cut(q, 1.0, seed=s)[0] for s in range(400)], axis=0)
+    m1, v1 = t.enumerate_cut(q, 1.0)
+    assert np.all(np.abs(est - m1) <= 5 * np.sqrt(v1 / 400) + 1e-12 * np.abs(m1))
