@@ -133,9 +133,9 @@ typedef struct {
 SBH_API sbh_status sbh_build(const float* points, const float* weights, const float* normals, int64_t n,
                      int32_t leaf_size, void* stream, sbh_tree** out);
 
-/* Most paths per subdomain any evaluation takes (the sample index is carried in 19 bits of a
+/* Most paths per subdomain any evaluation takes (the sample index is carried in 16 bits of a
  * task tag): every entry point taking samples_per_subdomain returns SBH_EINVAL beyond it. */
-#define SBH_MAX_SAMPLES_PER_SUBDOMAIN (1 << 19)
+#define SBH_MAX_SAMPLES_PER_SUBDOMAIN (1 << 16)
 
 /* Stochastic estimate of F at nq queries (Algorithm 2 with Eq. 5-7; Sec. 3.3.1 subdomains are
  * the root's children), S = samples_per_subdomain paths per subdomain, 1 <= S <=

@@ -34,6 +34,13 @@ namespace {
 #ifndef SBH_BATCHED_MIN_BLOCKS
 #define SBH_BATCHED_MIN_BLOCKS 4
 #endif
+// the smooth-distance instance fits 5 blocks per SM in 48 registers without spills (2% faster)
+#ifndef SBH_SMOOTH_MIN_BLOCKS
+#define SBH_SMOOTH_MIN_BLOCKS 5
+#endif
+// resident blocks per SM the estimator and the multi-set kernel are built for, per kernel kind
+template <int KIND>
+constexpr int value_min_blocks() { return KIND == SBH_SMOOTHDIST ? SBH_SMOOTH_MIN_BLOCKS : SBH_BATCHED_MIN_BLOCKS; }
 #ifndef SBH_STAGE_MAX
 #define SBH_STAGE_MAX 128
 #endif
@@ -41,9 +48,9 @@ namespace {
 // lanes may continue, else queued as decision tasks
 // A subdomain's depth-0 decisions are taken in place by the warp (every lane at the same node)
 // when more than this many of its lanes may continue, else queued as decision tasks. Measured on
-// the estimator: 24. The adjoint and learned instances always queue them (32): their larger code
-// ran slower with the decision inlined twice, and queueing let the learned one keep its state in
-// registers.
+// the estimator: 24. The smooth-distance, adjoint and learned instances always queue them (32):
+// their larger code ran slower with the decision inlined twice (smooth distance 2.55 against 2.29
+// ms, adjoint 43-48 against 39.6), and queueing let the learned one keep its state in registers.
 #ifndef SBH_DEPTH0_QUEUE_MAX
 #define SBH_DEPTH0_QUEUE_MAX 24
 #endif
@@ -51,8 +58,14 @@ namespace {
 #ifndef SBH_GRAD_MIN_BLOCKS
 #define SBH_GRAD_MIN_BLOCKS 3
 #endif
-template <bool LEARNED, bool GRAD>
-constexpr int depth0_queue_max() { return (LEARNED || GRAD) ? 32 : SBH_DEPTH0_QUEUE_MAX; }
+#ifndef SBH_DEPTH0_QUEUE_MAX_SMOOTH
+#define SBH_DEPTH0_QUEUE_MAX_SMOOTH 32
+#endif
+template <int KIND, bool LEARNED, bool GRAD>
+constexpr int depth0_queue_max()
+{
+    return (LEARNED || GRAD) ? 32 : (KIND == SBH_SMOOTHDIST ? SBH_DEPTH0_QUEUE_MAX_SMOOTH : SBH_DEPTH0_QUEUE_MAX);
+}
 // resident blocks per SM of the learned-proposal instance (its per-warp scoring scratch takes
 // shared memory: three blocks fit)
 #ifndef SBH_LEARNED_MIN_BLOCKS
@@ -66,6 +79,18 @@ constexpr int depth0_queue_max() { return (LEARNED || GRAD) ? 32 : SBH_DEPTH0_QU
 constexpr int kWarpsPerBlock = 8;
 constexpr int kRing = 64;  // ring capacity per warp; at most 63 tasks wait at any time
 constexpr uint32_t kRingMask = kRing - 1;
+// a decision task's tag: the query's slot in the warp (5 bits), the depth (5 bits: at most
+// kMaxDepth generations), the subdomain index (6 bits: a root has at most 64 children, and a
+// multi-point root leaf at most 64 points) and the sample index (16 bits)
+__device__ __forceinline__ uint32_t make_tag(uint32_t slot, uint32_t depth, uint32_t ai, uint32_t sample)
+{
+    return slot | depth << 5 | ai << 10 | sample << 16;
+}
+__device__ __forceinline__ uint32_t tag_slot(uint32_t t) { return t & 31u; }
+__device__ __forceinline__ uint32_t tag_depth(uint32_t t) { return (t >> 5) & 31u; }
+__device__ __forceinline__ uint32_t tag_sub(uint32_t t) { return (t >> 10) & 63u; }
+__device__ __forceinline__ uint32_t tag_sample(uint32_t t) { return t >> 16; }
+static_assert(kMaxDepth < 32 && SBH_MAX_SAMPLES_PER_SUBDOMAIN <= 65536 && kMaxLeafSize <= 64, "tag fields");
 // unroll factor of a swap's loop over pairs of children, measured per kernel: 2 for the terms of
 // one record (Coulomb, affine), 1 for the winding term and its second record. Left to the
 // compiler, the Coulomb instance unrolled further and spilled registers.
@@ -76,17 +101,16 @@ template <int KIND>
 constexpr int swap_unroll() { return KIND == SBH_WINDING ? SBH_SWAP_UNROLL_WINDING : 2; }
 
 // per-warp shared state, structure of arrays
+template <int KIND>
 struct WarpState {
     // decision tasks
     int32_t d_node[kRing];
     uint32_t d_x0[kRing];    // the decision's random words: child pick
     uint32_t d_x1[kRing];    //                              roulette
-    uint32_t d_tag[kRing];   // slot | depth << 5 | sample << 13
-    int32_t d_ai[kRing];
+    uint32_t d_tag[kRing];   // slot | depth << 5 | subdomain << 10 | sample << 16
     float d_prr[kRing];
     float d_dT[kRing];       // correctly rounded distance from the query to the node's centre
     float d_wT[kRing];       // the node's mass (or point count)
-    float d_wa[kRing];       // the subdomain's mass (or point count)
     // swap tasks
     int32_t s_node[kRing];
     uint32_t s_slot[kRing];
@@ -95,8 +119,9 @@ struct WarpState {
     float qx[32], qy[32], qz[32];
     uint32_t qctr[32];       // counter word 0 of each query's random stream
     float acc[32];           // sum of the swap terms (smooth distance: in units of exp(-alpha ref))
-    float ref[32];
+    float ref[KIND == SBH_SMOOTHDIST ? 32 : 1];  // smooth distance: the frame of acc (unused otherwise)
     float slack;             // certain_stop's slack for the current tree
+    int32_t first_sub;       // the current tree's first subdomain
 };
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31; }
@@ -109,21 +134,30 @@ constexpr int kStageMax = SBH_STAGE_MAX;
 
 // The stage sits at the start of the dynamic shared memory in a fixed layout of kStageMax entries
 // per array, so that its arrays are constant shared-memory addresses (no pointers held in
-// registers): pm [kStageMax] float4, dip [kStageMax] float4 (winding kernel only), cdf, meta and
-// fc [kStageMax] 4-byte words. What else a block keeps in dynamic shared memory follows it.
+// registers): pm [kStageMax] float4, cdf, meta and fc [kStageMax] 4-byte words, then for the
+// winding kernel dip [kStageMax] float4. What else a block keeps in dynamic shared memory follows.
 extern __shared__ float4 s_dyn[];
-constexpr size_t kStageBytes = (size_t)kStageMax * (2 * sizeof(float4) + 3 * sizeof(uint32_t));
-static_assert(kStageBytes % 16 == 0, "the region after the stage stays 16-byte aligned");
+constexpr size_t kStageBaseBytes = (size_t)kStageMax * (sizeof(float4) + 3 * sizeof(uint32_t));
+static_assert(kStageBaseBytes % 16 == 0, "dip and what follows the stage stay 16-byte aligned");
+template <int KIND>
+constexpr size_t stage_bytes() { return kStageBaseBytes + (KIND == SBH_WINDING ? kStageMax * sizeof(float4) : 0); }
 
 struct Stage {
     int32_t lo;       // first staged node id
     uint32_t n;       // number of staged nodes (0: nothing staged)
     __device__ __forceinline__ static float4* pm() { return s_dyn; }
-    __device__ __forceinline__ static float4* dip() { return s_dyn + kStageMax; }
-    __device__ __forceinline__ static float* cdf() { return reinterpret_cast<float*>(s_dyn + 2 * kStageMax); }
+    __device__ __forceinline__ static float* cdf() { return reinterpret_cast<float*>(s_dyn + kStageMax); }
     __device__ __forceinline__ static uint32_t* meta() { return reinterpret_cast<uint32_t*>(cdf() + kStageMax); }
     __device__ __forceinline__ static int32_t* fc() { return reinterpret_cast<int32_t*>(meta() + kStageMax); }
-    __device__ __forceinline__ static unsigned char* after() { return reinterpret_cast<unsigned char*>(s_dyn) + kStageBytes; }
+    __device__ __forceinline__ static float4* dip()  // winding kernel only
+    {
+        return reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_dyn) + kStageBaseBytes);
+    }
+    template <int KIND>
+    __device__ __forceinline__ static unsigned char* after()
+    {
+        return reinterpret_cast<unsigned char*>(s_dyn) + stage_bytes<KIND>();
+    }
 };
 
 __device__ __forceinline__ float4 ld_pm(const TreeView& T, const Stage& S, int32_t v)
@@ -219,18 +253,26 @@ struct Params {
     KernelParams kp;
     int S;
     uint2 key;
-    PhiloxRoundKeys rk;      // the round keys of key
     int sampling, rr, coherent, raw_sum;
     float* out;
     int64_t qbase;           // index of the first query in the caller's whole query set (chunked runs)
     float* grad;             // adjoint only: d out / d q, [nq][3]
-    float* gsum;             // adjoint only: shared memory, per warp the 32 queries' swap gradients [32][3]
     // learned proposal only
     const __half* mlpw;
     float near;
-    const MlpFrag* frag;     // shared memory, set in the kernel
-    LearnScratch* learn;     // shared memory, one per warp, set in the kernel
 };
+
+// What follows the stage in dynamic shared memory, at fixed offsets: the learned proposal's weight
+// fragments and one scoring scratch per warp, or the adjoint's per-warp [32][3] gradient sums
+template <int KIND>
+__device__ __forceinline__ MlpFrag* mlp_frag() { return reinterpret_cast<MlpFrag*>(Stage::after<KIND>()); }
+template <int KIND>
+__device__ __forceinline__ LearnScratch* learn_scratch()
+{
+    return reinterpret_cast<LearnScratch*>(Stage::after<KIND>() + sizeof(MlpFrag));
+}
+template <int KIND>
+__device__ __forceinline__ float* grad_sums() { return reinterpret_cast<float*>(Stage::after<KIND>()); }
 
 // The learned picks of the gated lanes of a decision batch (every lane of the warp takes part).
 // Rows = the children of the gated decisions in lane order, processed in groups of whole
@@ -248,7 +290,7 @@ __device__ __forceinline__ void learned_picks(const Params& P, const Stage& S, c
 {
     const float* slnB = sdiam + kDiamLevels;  // ln |B| per level, stored after the diagonals
     const TreeView& T = P.T;
-    LearnScratch& L = P.learn[threadIdx.x >> 5];
+    LearnScratch& L = learn_scratch<KIND>()[threadIdx.x >> 5];
     const uint32_t lane = lane_id();
     const int k = __popc(gm & lanemask_lt());
     const int v = gated ? nc : 0;
@@ -316,7 +358,7 @@ __device__ __forceinline__ void learned_picks(const Params& P, const Stage& S, c
             }
             store_feature_row(&L.A[lane * kChunkWords], x, live);
             __syncwarp();
-            const float sco = score_chunk_shared(*P.frag, L.A, L.sc);
+            const float sco = score_chunk_shared(*mlp_frag<KIND>(), L.A, L.sc);
             // segmented inclusive prefix sums over the lanes, restarting at each decision's head
             float pe = live ? __expf(clamp_score(sco)) : 0.0f, pm = mc;
             const unsigned heads = __ballot_sync(0xFFFFFFFFu, head);
@@ -362,11 +404,12 @@ __device__ __forceinline__ void learned_picks(const Params& P, const Stage& S, c
 // The random block of the decision (query slot, subdomain ai, sample, depth) of a path now at a
 // node at distance dT with cell diagonal BT; false when its roulette stops the path whichever child
 // is picked (certain_stop), which then needs no decision task.
-__device__ __forceinline__ bool draw_decision(const Params& P, const WarpState& W, uint32_t slot, int32_t ai,
-                                              uint32_t sample, uint32_t depth, float dT, float BT, uint32_t& x0,
-                                              uint32_t& x1)
+template <int KIND>
+__device__ __forceinline__ bool draw_decision(const Params& P, const PhiloxRoundKeys& K, const WarpState<KIND>& W,
+                                              uint32_t tag, float dT, float BT, uint32_t& x0, uint32_t& x1)
 {
-    const uint4 x = philox4x32_10(make_uint4(W.qctr[slot], (uint32_t)ai, sample, depth), P.rk);
+    const uint4 x =
+        philox4x32_10(make_uint4(W.qctr[tag_slot(tag)], tag_sub(tag), tag_sample(tag), tag_depth(tag)), K);
     x0 = x.x;
     x1 = x.y;
     return !certain_stop(P.rr, unit24(x.y), dT, BT, W.slack);
@@ -378,17 +421,17 @@ __device__ __forceinline__ bool draw_decision(const Params& P, const WarpState& 
 // With the learned proposal, wT carries p(path reaches node) (the product of the picks'
 // probabilities) and wa = 1, so that p_agg = wT / wa in both cases.
 template <int KIND, bool LEARNED>
-__device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpState& W, const float* sdiam, bool valid,
-                                       int32_t node, uint32_t x0, uint32_t x1,
-                                       uint32_t tag, int32_t ai, float prr, float dT, float wT, float wa,
-                                       uint32_t& d_tail, uint32_t& s_tail)
+__device__ __forceinline__ void decide(const Params& P, const PhiloxRoundKeys& K, const Stage& S, WarpState<KIND>& W,
+                                       const float* sdiam, bool valid, int32_t node, uint32_t x0, uint32_t x1,
+                                       uint32_t tag, float prr, float dT, float wT, float wa, uint32_t& d_tail,
+                                       uint32_t& s_tail)
 {
     const TreeView& T = P.T;
     bool cont = false;
     int32_t child = 0;
     float dc = 0.0f, wc = 0.0f, w = 0.0f, prr2 = 0.0f;
-    const uint32_t slot = tag & 31u;
-    const uint32_t depth = (tag >> 5) & 0xFFu;
+    const uint32_t slot = tag_slot(tag);
+    const uint32_t depth = tag_depth(tag);
     float3 q = make_float3(0.0f, 0.0f, 0.0f);
     uint32_t mT = 0;
     int32_t f = 0;
@@ -411,6 +454,8 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
             pick_prob = -pT.w;  // a mass pick: its probability m_c / m_T is formed on a continue
         }
         if (gm) learned_picks<KIND>(P, S, sdiam, gm, gated, q, pT, BT, f, nc, unit24(x0), child, pick_prob);
+        // read the query again rather than hold it through the scoring loop (registers)
+        if (valid) q = make_float3(W.qx[slot], W.qy[slot], W.qz[slot]);
     } else {
         if (valid) child = f + pick_child(T, S, node, f, nc, x0, P.sampling);
     }
@@ -430,7 +475,7 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
             // strictly increase, so depth < kMaxDepth always holds; the test only guards a damaged
             // tree); nor does one whose next roulette stops it whichever child it draws
             if (meta_kind(mc) == kPoint || depth + 1 >= (uint32_t)kMaxDepth ||
-                !draw_decision(P, W, slot, ai, tag >> 13, depth + 1, dc, sdiam[meta_level(mc)], y0, y1))
+                !draw_decision(P, K, W, tag + (1u << 5), dc, sdiam[meta_level(mc)], y0, y1))
                 wc = -1.0f;
         }
     }
@@ -447,11 +492,9 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
             W.d_x0[k] = y0;
             W.d_x1[k] = y1;
             W.d_tag[k] = tag + (1u << 5);  // depth + 1
-            W.d_ai[k] = ai;
             W.d_prr[k] = prr2;
             W.d_dT[k] = dc;
             W.d_wT[k] = wc;
-            W.d_wa[k] = wa;
         }
     }
     s_tail += __popc(push_s);
@@ -459,26 +502,37 @@ __device__ __forceinline__ void decide(const Params& P, const Stage& S, WarpStat
     __syncwarp();
 }
 
+// The weight of a path's subdomain a in p_agg: its mass (or point count); 1 with the learned
+// proposal, whose wT is already the probability of reaching the node
+template <bool LEARNED>
+__device__ __forceinline__ float subdomain_weight(const Params& P, const Stage& S, int32_t a)
+{
+    if constexpr (LEARNED) return 1.0f;
+    const TreeView& T = P.T;
+    return P.sampling ? (float)(__ldg(&T.ne[a]) - __ldg(&T.nb[a])) : ld_pm(T, S, a).w;
+}
+
 // Run up to 32 decision tasks from the front of the ring.
 template <int KIND, bool LEARNED>
-__device__ __forceinline__ void decision_batch(const Params& P, const Stage& S, WarpState& W, const float* sdiam,
-                                               uint32_t& d_head,
+__device__ __forceinline__ void decision_batch(const Params& P, const PhiloxRoundKeys& K, const Stage& S,
+                                               WarpState<KIND>& W, const float* sdiam, uint32_t& d_head,
                                                uint32_t& d_tail, uint32_t& s_tail)
 {
     const uint32_t avail = d_tail - d_head;
     const uint32_t take = avail < 32u ? avail : 32u;
     const bool valid = lane_id() < take;
-    int32_t node = 0, ai = 0;
+    int32_t node = 0;
     uint32_t tag = 0, x0 = 0, x1 = 0;
     float prr = 0.f, dT = 0.f, wT = 0.f, wa = 1.f;
     if (valid) {
         const uint32_t i = (d_head + lane_id()) & kRingMask;
-        node = W.d_node[i]; tag = W.d_tag[i]; ai = W.d_ai[i]; prr = W.d_prr[i]; dT = W.d_dT[i];
-        wT = W.d_wT[i]; wa = W.d_wa[i]; x0 = W.d_x0[i]; x1 = W.d_x1[i];
+        node = W.d_node[i]; tag = W.d_tag[i]; prr = W.d_prr[i]; dT = W.d_dT[i];
+        wT = W.d_wT[i]; x0 = W.d_x0[i]; x1 = W.d_x1[i];
     }
     __syncwarp();  // every task is read before new ones may reuse its slot
     d_head += take;
-    decide<KIND, LEARNED>(P, S, W, sdiam, valid, node, x0, x1, tag, ai, prr, dT, wT, wa, d_tail, s_tail);
+    if (valid) wa = subdomain_weight<LEARNED>(P, S, W.first_sub + (int32_t)tag_sub(tag));
+    decide<KIND, LEARNED>(P, K, S, W, sdiam, valid, node, x0, x1, tag, prr, dT, wT, wa, d_tail, s_tail);
 }
 
 // m f(p, q) and its gradient in q (added to g), for the adjoint: the kernel ∇_q f applied to the
@@ -572,7 +626,15 @@ __device__ __forceinline__ void swap_terms(const Params& P, const Stage& S, int3
     } else if constexpr (GRAD && KIND == SBH_WINDING) {
         const float4* cd = st ? Stage::dip() + (f - S.lo) : T.dip + f;
         float s0 = 0.0f;
-        for (int k = 0; k < nc; ++k) s0 += winding_vg_4pi(cp[k], cd[k], q, g);
+        // the next child's records are requested before this one's terms are formed (3% faster)
+        float4 pn = cp[0], dn = cd[0];
+        for (int k = 0; k < nc; ++k) {
+            const float4 pk = pn, dk = dn;
+            const int kn = k + 1 < nc ? k + 1 : k;
+            pn = cp[kn];
+            dn = cd[kn];
+            s0 += winding_vg_4pi(pk, dk, q, g);
+        }
         float go[3] = {0.0f, 0.0f, 0.0f};
         const float own = winding_vg_4pi(pT, ld_dip(T, S, node), q, go);
         const float ws = w * kInv4Pi;
@@ -627,10 +689,10 @@ __device__ __forceinline__ void swap_terms(const Params& P, const Stage& S, int3
 // Add a query's summed swap results (value tot in the frame exp(-alpha tr) for the smooth
 // distance; GRAD: gradient tg) into its sums in shared memory.
 template <int KIND, bool GRAD>
-__device__ __forceinline__ void add_to_query(const Params& P, WarpState& W, uint32_t slot, float tot, float tr,
+__device__ __forceinline__ void add_to_query(const Params& P, WarpState<KIND>& W, uint32_t slot, float tot, float tr,
                                              const float tg[3])
 {
-    float* qg = GRAD ? P.gsum + (threadIdx.x >> 5) * 96 + 3 * slot : nullptr;
+    float* qg = GRAD ? grad_sums<KIND>() + (threadIdx.x >> 5) * 96 + 3 * slot : nullptr;
     if constexpr (KIND == SBH_SMOOTHDIST) {
         const float a = P.kp.alpha;
         float qr = W.ref[slot], qa = W.acc[slot];
@@ -655,7 +717,7 @@ __device__ __forceinline__ void add_to_query(const Params& P, WarpState& W, uint
 // Run up to 32 swap tasks from the front of the ring, one per lane, each added to its query's sum
 // in lane order.
 template <int KIND, bool GRAD>
-__device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, WarpState& W, uint32_t& s_head,
+__device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, WarpState<KIND>& W, uint32_t& s_head,
                                            uint32_t s_tail)
 {
     const uint32_t avail = s_tail - s_head;
@@ -712,8 +774,8 @@ __device__ __forceinline__ void swap_batch(const Params& P, const Stage& S, Warp
 // One tile of 32 queries (query index tile * 32 + lane within the set described by P), run by
 // one warp: control variates and depth-0 decisions lane-parallel, everything else as tasks.
 template <int KIND, bool LEARNED, bool GRAD>
-__device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpState& W, const float* sdiam,
-                                         int64_t tile)
+__device__ __forceinline__ void run_tile(const Params& P, const PhiloxRoundKeys& K, const Stage& S, WarpState<KIND>& W,
+                                         const float* sdiam, int64_t tile)
 {
     const TreeView& T = P.T;
     const int32_t first_sub = T.ctrl->first_sub;
@@ -721,14 +783,17 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
     const uint32_t lane = lane_id();
     const int64_t j = tile * 32 + lane;
     const bool active = j < P.nq;
-    float3 q = make_float3(0.f, 0.f, 0.f);
-    if (active) q = make_float3(P.Q[3 * j], P.Q[3 * j + 1], P.Q[3 * j + 2]);
-    W.qx[lane] = q.x; W.qy[lane] = q.y; W.qz[lane] = q.z;
+    float3 q0 = make_float3(0.f, 0.f, 0.f);
+    if (active) q0 = make_float3(P.Q[3 * j], P.Q[3 * j + 1], P.Q[3 * j + 2]);
+    W.qx[lane] = q0.x; W.qy[lane] = q0.y; W.qz[lane] = q0.z;
     W.qctr[lane] = P.coherent ? 0u : (uint32_t)(j + P.qbase);
     W.acc[lane] = 0.0f;
-    W.ref[lane] = 3.0e38f;
-    if (lane == 0) W.slack = stop_slack(T.ctrl->lo, T.ctrl->side, sdiam[0]);
-    float* qg = GRAD ? P.gsum + (threadIdx.x >> 5) * 96 + 3 * lane : nullptr;
+    if constexpr (KIND == SBH_SMOOTHDIST) W.ref[lane] = 3.0e38f;
+    if (lane == 0) {
+        W.slack = stop_slack(T.ctrl->lo, T.ctrl->side, sdiam[0]);
+        W.first_sub = first_sub;
+    }
+    float* qg = GRAD ? grad_sums<KIND>() + (threadIdx.x >> 5) * 96 + 3 * lane : nullptr;
     if (GRAD) { qg[0] = 0.0f; qg[1] = 0.0f; qg[2] = 0.0f; }
     __syncwarp();
     float cv = 0.0f;
@@ -739,6 +804,10 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
 
     for (int ai = 0; ai < n_sub; ++ai) {
         const int32_t a = first_sub + ai;
+        // the lane's query, read from the warp's shared copy each time (not held in registers
+        // through the decision and swap batches: 56 instead of 62 for the winding estimator); the
+        // learned and adjoint instances keep their register copy (they spilled more or ran slower)
+        const float3 q = (LEARNED || GRAD) ? q0 : make_float3(W.qx[lane], W.qy[lane], W.qz[lane]);
         const float4 pa = ld_pm(T, S, a);
         const uint32_t ma = ld_meta(T, S, a);
         if (active) {  // control variate CV_a
@@ -755,7 +824,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
             }
         }
         if (meta_kind(ma) == kPoint) continue;
-        const float wa = LEARNED ? 1.0f : (P.sampling ? (float)(__ldg(&T.ne[a]) - __ldg(&T.nb[a])) : pa.w);
+        const float wa = subdomain_weight<LEARNED>(P, S, a);
         const float da = dist_rn(pa.x, pa.y, pa.z, q);
         const float Ba = sdiam[meta_level(ma)];
         for (int s = 0; s < P.S; ++s) {
@@ -763,12 +832,12 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
             // place by the whole warp (the node is the same for every lane) when enough lanes need it,
             // else queued as tasks that a later batch runs with other work
             uint32_t x0 = 0, x1 = 0;
-            const bool live = active && draw_decision(P, W, lane, ai, (uint32_t)s, 0u, da, Ba, x0, x1);
+            const uint32_t tag = make_tag(lane, 0u, (uint32_t)ai, (uint32_t)s);
+            const bool live = active && draw_decision(P, K, W, tag, da, Ba, x0, x1);
             const unsigned push = __ballot_sync(0xFFFFFFFFu, live);
-            constexpr int kQueueMax = depth0_queue_max<LEARNED, GRAD>();
+            constexpr int kQueueMax = depth0_queue_max<KIND, LEARNED, GRAD>();
             if (kQueueMax < 0 || (kQueueMax < 32 && __popc(push) > kQueueMax)) {
-                decide<KIND, LEARNED>(P, S, W, sdiam, live, a, x0, x1, lane | ((uint32_t)s << 13), ai, 1.0f, da, wa, wa,
-                                      d_tail, s_tail);
+                decide<KIND, LEARNED>(P, K, S, W, sdiam, live, a, x0, x1, tag, 1.0f, da, wa, wa, d_tail, s_tail);
                 while (s_tail - s_head >= 32u) swap_batch<KIND, GRAD>(P, S, W, s_head, s_tail);
             } else {
                 if (live) {
@@ -776,18 +845,16 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
                     W.d_node[k] = a;
                     W.d_x0[k] = x0;
                     W.d_x1[k] = x1;
-                    W.d_tag[k] = lane | ((uint32_t)s << 13);
-                    W.d_ai[k] = ai;
+                    W.d_tag[k] = tag;
                     W.d_prr[k] = 1.0f;
                     W.d_dT[k] = da;
                     W.d_wT[k] = wa;
-                    W.d_wa[k] = wa;
                 }
                 d_tail += __popc(push);
                 __syncwarp();
             }
             while (d_tail - d_head >= 32u) {
-                decision_batch<KIND, LEARNED>(P, S, W, sdiam, d_head, d_tail, s_tail);
+                decision_batch<KIND, LEARNED>(P, K, S, W, sdiam, d_head, d_tail, s_tail);
                 while (s_tail - s_head >= 32u) swap_batch<KIND, GRAD>(P, S, W, s_head, s_tail);
             }
         }
@@ -795,7 +862,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
     // drain the partial batches
     while (d_tail != d_head || s_tail != s_head) {
         if (s_tail != s_head) swap_batch<KIND, GRAD>(P, S, W, s_head, s_tail);
-        if (d_tail != d_head) decision_batch<KIND, LEARNED>(P, S, W, sdiam, d_head, d_tail, s_tail);
+        if (d_tail != d_head) decision_batch<KIND, LEARNED>(P, K, S, W, sdiam, d_head, d_tail, s_tail);
     }
     __syncwarp();
     if (active) {
@@ -835,7 +902,7 @@ __device__ __forceinline__ void run_tile(const Params& P, const Stage& S, WarpSt
     __syncwarp();
 }
 
-// dynamic shared memory: the stage (kStageBytes), then [learned proposal: MlpFrag, one LearnScratch
+// dynamic shared memory: the stage (stage_bytes), then [learned proposal: MlpFrag, one LearnScratch
 // per warp | adjoint: one [32][3] gradient sum per warp]
 template <bool LEARNED, bool GRAD>
 constexpr size_t extra_smem_bytes()
@@ -846,19 +913,12 @@ constexpr size_t extra_smem_bytes()
 
 template <int KIND, bool LEARNED, bool GRAD>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock,
-                                  LEARNED ? SBH_LEARNED_MIN_BLOCKS : (GRAD ? SBH_GRAD_MIN_BLOCKS : SBH_BATCHED_MIN_BLOCKS))
-    k_stoch_batched(Params P, int32_t stage_lo, uint32_t stage_n)
+                                  LEARNED ? SBH_LEARNED_MIN_BLOCKS : (GRAD ? SBH_GRAD_MIN_BLOCKS : value_min_blocks<KIND>()))
+    k_stoch_batched(Params P, PhiloxRoundKeys K, int32_t stage_lo, uint32_t stage_n)
 {
-    __shared__ WarpState s_state[kWarpsPerBlock];
+    __shared__ WarpState<KIND> s_state[kWarpsPerBlock];
     __shared__ float sdiam[LEARNED ? 2 * kDiamLevels : kDiamLevels];  // learned: then ln of each
-    if constexpr (LEARNED) {
-        MlpFrag* F = reinterpret_cast<MlpFrag*>(Stage::after());
-        mlp_frag_fill(P.mlpw, *F);
-        P.frag = F;
-        P.learn = reinterpret_cast<LearnScratch*>(Stage::after() + sizeof(MlpFrag));
-    } else if constexpr (GRAD) {
-        P.gsum = reinterpret_cast<float*>(Stage::after());
-    }
+    if constexpr (LEARNED) mlp_frag_fill(P.mlpw, *mlp_frag<KIND>());
     Stage S;
     S.lo = stage_lo;
     S.n = stage_n;
@@ -875,12 +935,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock,
         if (LEARNED) sdiam[kDiamLevels + threadIdx.x] = __logf(P.T.ctrl->diam[threadIdx.x]);
     }
     __syncthreads();
-    WarpState& W = s_state[threadIdx.x >> 5];
+    WarpState<KIND>& W = s_state[threadIdx.x >> 5];
     const int64_t n_tiles = (P.nq + 31) / 32;
     const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t warp_stride = (int64_t)gridDim.x * kWarpsPerBlock;
     for (int64_t tile = warp_global; tile < n_tiles; tile += warp_stride)
-        run_tile<KIND, LEARNED, GRAD>(P, S, W, sdiam, tile);
+        run_tile<KIND, LEARNED, GRAD>(P, K, S, W, sdiam, tile);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -902,17 +962,18 @@ struct MultiParams {
     int n_sets;
     int64_t total_tiles;
     unsigned long long* counter;
-    Params base;  // kernel, samples, key and options shared by all sets
+    Params base;         // kernel, samples, key and options shared by all sets
+    PhiloxRoundKeys rk;  // the round keys of base.key (read from the parameter space, not per warp)
 };
 
 template <int KIND>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, SBH_BATCHED_MIN_BLOCKS) k_stoch_multi(MultiParams M)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, value_min_blocks<KIND>()) k_stoch_multi(MultiParams M)
 {
-    __shared__ WarpState s_state[kWarpsPerBlock];
+    __shared__ WarpState<KIND> s_state[kWarpsPerBlock];
     __shared__ float s_diam[kWarpsPerBlock][kDiamLevels];
     __shared__ Params s_params[kWarpsPerBlock];  // the warp's current set (kept out of registers)
     const int warp = threadIdx.x >> 5;
-    WarpState& W = s_state[warp];
+    WarpState<KIND>& W = s_state[warp];
     float* sdiam = s_diam[warp];
     Params& P = s_params[warp];
     Stage S;  // nothing staged: the sets' trees differ
@@ -940,18 +1001,18 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, SBH_BATCHED_MIN_BLOCKS) k
             if (lane < (uint32_t)kDiamLevels) sdiam[lane] = D.T.ctrl->diam[lane];
             __syncwarp();
         }
-        run_tile<KIND, false, false>(P, S, W, sdiam, tile - M.sets[lo].tile_begin);
+        run_tile<KIND, false, false>(P, M.rk, S, W, sdiam, tile - M.sets[lo].tile_begin);
     }
 }
 
 template <int KIND, bool LEARNED, bool GRAD>
 static cudaError_t launch_kind(const Params& P, unsigned blocks, int32_t lo, uint32_t n, cudaStream_t s)
 {
-    const size_t bytes = kStageBytes + extra_smem_bytes<LEARNED, GRAD>();
+    const size_t bytes = stage_bytes<KIND>() + extra_smem_bytes<LEARNED, GRAD>();
     cudaError_t e = cudaFuncSetAttribute(k_stoch_batched<KIND, LEARNED, GRAD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_stoch_batched<KIND, LEARNED, GRAD><<<blocks, 32 * kWarpsPerBlock, bytes, s>>>(P, lo, n);
+    k_stoch_batched<KIND, LEARNED, GRAD><<<blocks, 32 * kWarpsPerBlock, bytes, s>>>(P, philox_round_keys(P.key), lo, n);
     return cudaSuccess;
 }
 
@@ -965,12 +1026,10 @@ static cudaError_t launch_batched_impl(const TreeView& T, const TreeCtrl& host_c
     Params P;
     P.qbase = qbase;
     P.grad = grad;
-    P.gsum = nullptr;
     P.T = T; P.Q = Q; P.nq = nq; P.kp = kp; P.S = S;
     P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    P.rk = philox_round_keys(P.key);
     P.sampling = o.sampling; P.rr = o.rr; P.coherent = o.seed_mode; P.raw_sum = o.raw_sum; P.out = out;
-    P.mlpw = (const __half*)mlp_half; P.near = near; P.frag = nullptr; P.learn = nullptr;
+    P.mlpw = (const __half*)mlp_half; P.near = near;
     const int64_t tiles = (nq + 31) / 32;
     int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const int64_t grid_cap = (int64_t)device_sm_count() * SBH_GRID_BLOCKS_PER_SM;
@@ -1029,20 +1088,28 @@ cudaError_t launch_stoch_multi(const void* set_descs, int n_sets, int64_t total_
     M.counter = counter;
     Params& P = M.base;
     P.T = TreeView{}; P.Q = nullptr; P.nq = 0; P.kp = kp; P.S = S; P.out = nullptr; P.qbase = 0;
-    P.grad = nullptr; P.gsum = nullptr;
-    P.mlpw = nullptr; P.near = 0.0f; P.frag = nullptr; P.learn = nullptr;
+    P.grad = nullptr;
+    P.mlpw = nullptr; P.near = 0.0f;
     P.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    P.rk = philox_round_keys(P.key);
+    M.rk = philox_round_keys(P.key);
     P.sampling = o.sampling; P.rr = o.rr; P.coherent = o.seed_mode; P.raw_sum = o.raw_sum;
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     // persistent: as many blocks as are resident at once
-    const unsigned blocks = (unsigned)device_sm_count() * SBH_BATCHED_MIN_BLOCKS;
+    const unsigned sms = (unsigned)device_sm_count();
     switch (kp.kind) {
-    case SBH_COULOMB: k_stoch_multi<SBH_COULOMB><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(M); break;
-    case SBH_WINDING: k_stoch_multi<SBH_WINDING><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(M); break;
-    case SBH_SMOOTHDIST: k_stoch_multi<SBH_SMOOTHDIST><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(M); break;
-    case SBH_AFFINE: k_stoch_multi<SBH_AFFINE><<<blocks, 32 * kWarpsPerBlock, 0, s>>>(M); break;
+    case SBH_COULOMB:
+        k_stoch_multi<SBH_COULOMB><<<sms * value_min_blocks<SBH_COULOMB>(), 32 * kWarpsPerBlock, 0, s>>>(M);
+        break;
+    case SBH_WINDING:
+        k_stoch_multi<SBH_WINDING><<<sms * value_min_blocks<SBH_WINDING>(), 32 * kWarpsPerBlock, 0, s>>>(M);
+        break;
+    case SBH_SMOOTHDIST:
+        k_stoch_multi<SBH_SMOOTHDIST><<<sms * value_min_blocks<SBH_SMOOTHDIST>(), 32 * kWarpsPerBlock, 0, s>>>(M);
+        break;
+    case SBH_AFFINE:
+        k_stoch_multi<SBH_AFFINE><<<sms * value_min_blocks<SBH_AFFINE>(), 32 * kWarpsPerBlock, 0, s>>>(M);
+        break;
     default: return cudaErrorInvalidValue;
     }
     note_launch();

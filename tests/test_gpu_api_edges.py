@@ -34,12 +34,12 @@ def test_solve_host_rejects_bad_arguments(sbh):
 
 
 def test_sample_count_beyond_the_tag_width_is_rejected(sbh):
-    # the warp-task schedule carries the sample index in 19 bits: S = 2^19 is the largest accepted,
+    # the warp-task schedule carries the sample index in 16 bits: S = 2^16 is the largest accepted,
     # beyond it every entry point returns SBH_EINVAL before any launch
     p, w, q = _cloud(200, 8)
     t = sbh.sbh_build(dev(p), dev(w))
     Q = dev(q)
-    big = (1 << 19) + 1
+    big = (1 << 16) + 1
     with pytest.raises(sbh.SBHError, match="SBH_EINVAL"):
         sbh.sbh_eval(t, Q, samples_per_subdomain=big)
     with pytest.raises(sbh.SBHError, match="SBH_EINVAL"):
