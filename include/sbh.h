@@ -115,6 +115,9 @@ typedef struct {
     double* com_mass64;    /* [n_nodes][4] the same in FP64, before rounding */
     float* dipole;         /* [n_nodes][3] sum_j m_j n_j (zeros without normals) */
     float* cdf;            /* [n_nodes] prefix fraction of the node's mass among its siblings */
+    uint8_t* guide;        /* [n_nodes] the child pick's guide entry of the node's slot j among its
+                            * parent's nc children: the number of the first nc - 1 siblings' cdf
+                            * values <= ceil(j 2^24 / nc) 2^-24 (0 at the root) */
 } sbh_tree_export_buffers;
 
 /* Build the tree over n sources (Sec. 3.1).

@@ -43,8 +43,11 @@
  *     m_c / m_T (or |T_c| / |T| for the paper's count-uniform choice), which gives
  *     p(I in T_{I,k}) = m_{I,k} / m_a exactly as drawing I up front with p(I=i) = m_i / m_a.
  *   - Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), key = (seed low 32,
- *     seed high 32), counter = (query index, subdomain index, sample index, depth k); word 0
- *     picks the child, word 1 drives Russian roulette; u = (x >> 8) * 2^-24.
+ *     seed high 32). A decision needs two independent uniforms and a block gives four, so one
+ *     block serves two consecutive depths: the decision at depth k uses the block of counter
+ *     (query index, subdomain index, sample index, k - k mod 2), words 0 and 1 at even k, words
+ *     2 and 3 at odd k. The first of the two words picks the child, the second drives Russian
+ *     roulette; u = (x >> 8) * 2^-24.
  *   - Child pick: the stored FP32 prefix fraction cdf_c = (sum_{c'<=c} m_c') / m_T (the last
  *     child's is exactly 1); the chosen child is the number of children c < last with
  *     cdf_c <= u.
@@ -95,6 +98,17 @@ SBHO_API void sbho_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], u
 
 /* uniform in [0,1) with 24 random bits: exactly representable in FP32 and FP64 */
 static float unit24f(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+
+/* The two random words of the decision at depth k of the path (query index qc, subdomain ai,    */
+/* sample s): block (qc, ai, s, k - k mod 2), words 0 and 1 at even k, 2 and 3 at odd k.         */
+static void decision_words(const uint32_t key[2], uint32_t qc, uint32_t ai, uint32_t s, uint32_t k, uint32_t w[2])
+{
+    const uint32_t ctr[4] = {qc, ai, s, k & ~1u};
+    uint32_t x[4];
+    sbho_philox4x32_10(ctr, key, x);
+    w[0] = x[2 * (k & 1u)];
+    w[1] = x[2 * (k & 1u) + 1];
+}
 
 /* ------------------------------------------------------------------------------------------ */
 /* Kernels f(p, q) times the source weight, in FP64 (Sec. 3 Eq. 1; Sec. 4.2 Coulomb-like       */
@@ -787,9 +801,9 @@ SBHO_API void sbho_bh(const void *h, const sbho_kernel *k, const float *queries,
 /*     CV_a = m_a f(p_a, q);  F_a = 0                                                          */
 /*     for s in 1..S: T = a, k = 0, p_rr = 1                                                   */
 /*       while T is not a leaf:                                                                */
-/*         c   = child of T containing I            (drawn lazily, word 0)                     */
+/*         c   = child of T containing I            (drawn lazily, first word)                 */
 /*         p   = Eq. 5 for (T, c); stop unless      (exact test rand < p on FP32 inputs,       */
-/*               rand < p                            word 1)                                    */
+/*               rand < p                            second word)                               */
 /*         Delta = Eq. 6 at T;  p_agg = p(I in T);  p_rr *= p                                  */
 /*         F_a += Delta / (p_agg p_rr);  T = c;  k += 1                                        */
 /*     F += CV_a + F_a / S                                                                     */
@@ -826,9 +840,9 @@ SBHO_API void sbho_replay(const void *h, const sbho_kernel *k, const float *quer
                 uint32_t depth = 0;
                 double prr = 1.0;
                 while (t->nchild[T] > 0) {
-                    uint32_t ctr[4] = {coherent ? 0u : (qidx ? qidx[j] : (uint32_t)j), (uint32_t)ai, (uint32_t)s, depth};
-                    uint32_t x[4];
-                    sbho_philox4x32_10(ctr, key, x);
+                    uint32_t x[2];
+                    decision_words(key, coherent ? 0u : (qidx ? qidx[j] : (uint32_t)j), (uint32_t)ai, (uint32_t)s,
+                                   depth, x);
                     int64_t c = pick_child(t, T, x[0], sampling);
                     float p;
                     if (!rr_continue32(t, T, c, q32, rr, unit24f(x[1]), &p)) break;
@@ -884,9 +898,9 @@ SBHO_API void sbho_replay_grad(const void *h, const sbho_kernel *k, const float 
                 uint32_t depth = 0;
                 double prr = 1.0;
                 while (t->nchild[T] > 0) {
-                    uint32_t ctr[4] = {coherent ? 0u : (qidx ? qidx[j] : (uint32_t)j), (uint32_t)ai, (uint32_t)s, depth};
-                    uint32_t x[4];
-                    sbho_philox4x32_10(ctr, key, x);
+                    uint32_t x[2];
+                    decision_words(key, coherent ? 0u : (qidx ? qidx[j] : (uint32_t)j), (uint32_t)ai, (uint32_t)s,
+                                   depth, x);
                     int64_t ch = pick_child(t, T, x[0], sampling);
                     float p;
                     if (!rr_continue32(t, T, ch, q32, rr, unit24f(x[1]), &p)) break;
@@ -960,8 +974,8 @@ SBHO_API void sbho_enumerate_grad(const void *h, const sbho_kernel *k, const flo
 /* Subdomains taken per query as the Barnes-Hut contribution nodes at beta_s (Sec. 3.3.1 names  */
 /* this cover as an alternative to the root's children): Algorithm 1's walk with parameter      */
 /* beta_s gives nodes that partition the sources; each one gets its control variate and one path */
-/* of Algorithm 2 started from it (Philox counter (query, index of the node in the walk's order, */
-/* 0, depth)). An oracle-only study of the paper's alternative; the CUDA path does not build it. */
+/* of Algorithm 2 started from it (the decisions' words as in sbho_replay, with the node's index */
+/* in the walk's order for the subdomain index and sample 0). An oracle-only study of the paper's alternative; the CUDA path does not build it. */
 /* work[j] counts the walk's far-field tests, plus a swap's children and node for every swap.    */
 /* ------------------------------------------------------------------------------------------ */
 static void bh_cut(const otree *t, int64_t v, const float q32[3], float beta, int64_t *out, int64_t *n,
@@ -994,8 +1008,8 @@ SBHO_API void sbho_replay_cut(const void *h, const sbho_kernel *k, const float *
                 double prr = 1.0;
                 F += node_term(t, k, a, q);
                 while (t->nchild[T] > 0) {
-                    uint32_t ctr[4] = {(uint32_t)j, (uint32_t)ai, 0u, depth}, x[4];
-                    sbho_philox4x32_10(ctr, key, x);
+                    uint32_t x[2];
+                    decision_words(key, (uint32_t)j, (uint32_t)ai, 0u, depth, x);
                     int64_t c = pick_child(t, T, x[0], SAMPLE_MASS);
                     float p;
                     if (!rr_continue32(t, T, c, q32, RR_PAPER, unit24f(x[1]), &p)) break;

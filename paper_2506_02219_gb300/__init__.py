@@ -67,7 +67,7 @@ class _Meta(C.Structure):
 
 class _Export(C.Structure):
     _fields_ = [(name, C.c_void_p) for name in ("perm", "code", "begin", "end", "first_child", "nchild", "level",
-                                                 "parent", "com_mass", "com_mass64", "dipole", "cdf")]
+                                                 "parent", "com_mass", "com_mass64", "dipole", "cdf", "guide")]
 
 
 _lock = threading.Lock()
@@ -500,7 +500,7 @@ def sbh_tree_export(tree: Tree, which: int = 0) -> dict:
          "end": np.zeros(N, np.int32), "first_child": np.zeros(N, np.int32), "nchild": np.zeros(N, np.int32),
          "level": np.zeros(N, np.int32), "parent": np.zeros(N, np.int32), "com_mass": np.zeros((N, 4), np.float32),
          "com_mass64": np.zeros((N, 4), np.float64), "dipole": np.zeros((N, 3), np.float32),
-         "cdf": np.zeros(N, np.float32)}
+         "cdf": np.zeros(N, np.float32), "guide": np.zeros(N, np.uint8)}
     e = _Export()
     for name, arr in a.items():
         setattr(e, name, arr.ctypes.data_as(C.c_void_p))

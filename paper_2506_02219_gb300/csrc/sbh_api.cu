@@ -146,7 +146,7 @@ sbh_status sbh_build(const float* points, const float* weights, const float* nor
     T->has_normals = normals != nullptr;
     T->stream = s;
     cudaGetDevice(&T->device);
-    cudaError_t e = sbh::alloc_tree(T->t4, n, normals != nullptr, false, s);
+    cudaError_t e = sbh::alloc_tree(T->t4, n, normals != nullptr, false, normals != nullptr, s);
     if (e == cudaSuccess) e = sbh::dalloc((void**)&T->t2.ctrl, sizeof(sbh::TreeCtrl), s);
     if (e != cudaSuccess) {
         release(T, s);
@@ -791,7 +791,7 @@ sbh_status sbh_eval_bh(sbh_tree* tree, const float* queries, int64_t nq, sbh_ker
     cudaStream_t s = (cudaStream_t)stream;
     if (!tree->t2.built) {
         // the root cube of t2.ctrl was written by sbh_build; alloc_tree keeps that block
-        cudaError_t e = sbh::alloc_tree(tree->t2, tree->n, tree->has_normals != 0, true, s);
+        cudaError_t e = sbh::alloc_tree(tree->t2, tree->n, tree->has_normals != 0, true, false, s);
         if (e == cudaSuccess) e = sbh::build_tree(tree, tree->t2, tree->lcp2, sbh::kMaxLevel2, 1, true, s);
         if (e != cudaSuccess) {  // give back what was taken, keep the control block with the root cube
             sbh::TreeCtrl* ctrl = tree->t2.ctrl;
@@ -900,6 +900,7 @@ sbh_status sbh_tree_export(const sbh_tree* tree, int32_t which, const sbh_tree_e
     cp(buf->parent, D.parent, N * sizeof(int32_t));
     cp(buf->com_mass, D.pm, N * sizeof(float4));
     cp(buf->cdf, D.cdf, N * sizeof(float));
+    cp(buf->guide, D.gd, N * sizeof(uint8_t));
     uint32_t* meta_h = nullptr;
     double* agg_h = nullptr;
     float4* dip_h = nullptr;

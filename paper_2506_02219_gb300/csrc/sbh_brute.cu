@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kBruteThreads) k_brute_grad(const float* __res
             const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
             if constexpr (KIND == SBH_COULOMB) {
                 const float e = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, kp.eps2)));
-                const float ir = rsqrtf(e);
+                const float ir = rsqrt_ftz(e);
                 const float t = pm.w * ir;
                 const float c = t * ir * ir;
                 v += t;
@@ -114,8 +114,8 @@ __global__ void __launch_bounds__(kBruteThreads) k_brute_grad(const float* __res
             } else if constexpr (KIND == SBH_WINDING) {
                 const float4 D = sdp[k];
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                if (r2 > 0.0f) {
-                    const float ir = rsqrtf(r2);
+                if (r2 >= kMinNormal) {
+                    const float ir = rsqrt_ftz(r2);
                     const float ir3 = ir * ir * ir;
                     const float dn = fmaf(dx, D.x, fmaf(dy, D.y, dz * D.z));
                     v = fmaf(kInv4Pi * dn, ir3, v);
@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(kBruteThreads) k_brute_grad(const float* __res
                 }
             } else if constexpr (KIND == SBH_SMOOTHDIST) {
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const float ir = rsqrtf(fmaxf(r2, 1e-37f));
+                const float ir = rsqrt_ftz(fmaxf(r2, 1e-37f));
                 const float r = r2 * ir;
                 if (r < ref) {
                     const float f = __expf(-kp.alpha * (ref - r));

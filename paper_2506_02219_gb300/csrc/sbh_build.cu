@@ -698,7 +698,7 @@ __global__ void k_pack(const double* __restrict__ agg, const int32_t* __restrict
                        const uint32_t* __restrict__ meta, const int32_t* __restrict__ nb,
                        const int32_t* __restrict__ parent, const float4* __restrict__ spw,
                        const float4* __restrict__ snrm, const TreeCtrl* __restrict__ ctrl, float4* __restrict__ pm,
-                       float4* __restrict__ dip, float* __restrict__ cdf)
+                       float4* __restrict__ dip, float4* __restrict__ pmd, float* __restrict__ cdf)
 {
     const int32_t N = ctrl->depth_base[ctrl->max_depth + 1];
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
@@ -716,6 +716,10 @@ __global__ void k_pack(const double* __restrict__ agg, const int32_t* __restrict
                                 __double2float_rn(a[3] / m), __double2float_rn(m));
             if (dip) dip[v] = make_float4(__double2float_rn(a[4]), __double2float_rn(a[5]), __double2float_rn(a[6]), 0.0f);
         }
+        if (pmd) {  // the same two records side by side, for one 32-byte load
+            pmd[2 * v] = pm[v];
+            pmd[2 * v + 1] = dip[v];
+        }
         if (v == 0) { cdf[0] = 1.0f; continue; }
         const int32_t par = parent[v];
         const int32_t f = fc[par];
@@ -724,6 +728,31 @@ __global__ void k_pack(const double* __restrict__ agg, const int32_t* __restrict
         double pre = 0.0;
         for (int32_t k = f; k <= v; ++k) pre += agg[8 * (int64_t)k];
         cdf[v] = __double2float_rn(pre / agg[8 * (int64_t)par]);
+    }
+}
+
+// The child pick's guide table (Chen and Asau's method), one entry per child slot: for slot j of
+// a node with nc children, the number of prefix fractions cdf_c <= u_j among the first nc - 1
+// children, where u_j = ceil(j 2^24 / nc) 2^-24 is the smallest 24-bit draw whose slot
+// floor(u nc) is j. It is stored at the child's own id (first child + j): every node but the root
+// fills one slot of its parent. That count never decreases with u, so a pick with draw u in slot
+// j that scans up from the entry finds the same child as counting all prefix fractions.
+__global__ void k_guide(const int32_t* __restrict__ fc, const uint32_t* __restrict__ meta,
+                        const int32_t* __restrict__ parent, const float* __restrict__ cdf,
+                        const TreeCtrl* __restrict__ ctrl, uint8_t* __restrict__ gd)
+{
+    const int32_t N = ctrl->depth_base[ctrl->max_depth + 1];
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < N; v += (int64_t)gridDim.x * blockDim.x) {
+        if (v == 0) { gd[0] = 0; continue; }
+        const int32_t par = parent[v];
+        const int32_t f = fc[par];
+        const uint32_t nc = meta_nchild(meta[par]);
+        const uint32_t j = (uint32_t)(v - f);
+        const uint32_t mj = (uint32_t)((((uint64_t)j << 24) + nc - 1u) / nc);  // < 2^24: exact in FP32
+        const float uj = (float)mj * 5.9604644775390625e-8f;
+        uint32_t cnt = 0;
+        for (uint32_t i = 0; i + 1u < nc; ++i) cnt += cdf[f + i] <= uj ? 1u : 0u;
+        gd[v] = (uint8_t)cnt;
     }
 }
 
@@ -792,13 +821,15 @@ struct ScratchSet {
     }
 };
 
-cudaError_t alloc_tree(DeviceTree& D, int64_t n, bool with_dip, bool with_skip, cudaStream_t s)
+cudaError_t alloc_tree(DeviceTree& D, int64_t n, bool with_dip, bool with_skip, bool with_rec, cudaStream_t s)
 {
     const int64_t cap = 2 * n + 1;
     D.cap = cap;  // D.ctrl is kept if the caller allocated it already
     SBH_TRY(dalloc((void**)&D.pm, cap * sizeof(float4), s));
     if (with_dip) SBH_TRY(dalloc((void**)&D.dip, cap * sizeof(float4), s));
+    if (with_dip && with_rec) SBH_TRY(dalloc((void**)&D.pmd, 2 * cap * sizeof(float4), s));
     SBH_TRY(dalloc((void**)&D.cdf, cap * sizeof(float), s));
+    SBH_TRY(dalloc((void**)&D.gd, cap * sizeof(uint8_t), s));
     SBH_TRY(dalloc((void**)&D.fc, cap * sizeof(int32_t), s));
     SBH_TRY(dalloc((void**)&D.meta, cap * sizeof(uint32_t), s));
     SBH_TRY(dalloc((void**)&D.nb, cap * sizeof(int32_t), s));
@@ -813,7 +844,7 @@ cudaError_t alloc_tree(DeviceTree& D, int64_t n, bool with_dip, bool with_skip, 
 
 void free_tree(DeviceTree& D, cudaStream_t s)
 {
-    dfree(D.pm, s); dfree(D.dip, s); dfree(D.cdf, s); dfree(D.fc, s); dfree(D.meta, s); dfree(D.nb, s);
+    dfree(D.pm, s); dfree(D.dip, s); dfree(D.pmd, s); dfree(D.cdf, s); dfree(D.gd, s); dfree(D.fc, s); dfree(D.meta, s); dfree(D.nb, s);
     dfree(D.ne, s); dfree(D.parent, s); dfree(D.skip, s); dfree(D.minl, s); dfree(D.agg, s); dfree(D.ctrl, s);
     D = DeviceTree();
 }
@@ -925,7 +956,9 @@ cudaError_t build_tree(sbh_tree* T, DeviceTree& D, const uint8_t* lcp, int max_l
         note_launch();
     }
     k_pack<<<grid_for(2 * n), kThreads, 0, s>>>(D.agg, D.fc, D.meta, D.nb, D.parent, T->spw, T->snrm, D.ctrl, D.pm,
-                                                D.dip, D.cdf);
+                                                D.dip, D.pmd, D.cdf);
+    note_launch();
+    k_guide<<<grid_for(2 * n), kThreads, 0, s>>>(D.fc, D.meta, D.parent, D.cdf, D.ctrl, D.gd);
     note_launch();
     k_finalize<<<1, 32, 0, s>>>(D.ctrl, D.fc, D.meta);
     note_launch();

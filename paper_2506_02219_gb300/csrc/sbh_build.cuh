@@ -15,7 +15,9 @@ struct DeviceTree {
     int level_shift = 0; // log2 of the per-dimension branching d: 2 or 1
     float4* pm = nullptr;
     float4* dip = nullptr;
+    float4* pmd = nullptr;   // [cap][2]: pm and dip interleaved (the estimator's tree with normals)
     float* cdf = nullptr;
+    uint8_t* gd = nullptr;
     int32_t* fc = nullptr;
     uint32_t* meta = nullptr;
     int32_t* nb = nullptr;
@@ -30,7 +32,7 @@ struct DeviceTree {
     TreeView view() const
     {
         TreeView v;
-        v.pm = pm; v.dip = dip; v.cdf = cdf; v.fc = fc; v.meta = meta; v.nb = nb; v.ne = ne;
+        v.pm = pm; v.dip = dip; v.pmd = pmd; v.cdf = cdf; v.gd = gd; v.fc = fc; v.meta = meta; v.nb = nb; v.ne = ne;
         v.skip = skip; v.ctrl = ctrl;
         return v;
     }
@@ -73,6 +75,6 @@ cudaError_t build_tree(sbh_tree* T, DeviceTree& D, const uint8_t* lcp, int max_l
 // Enqueue validation (sets *bad on the host after a sync), root cube, codes, sort and gather.
 cudaError_t build_sorted(sbh_tree* T, const float* pts, const float* w, const float* nrm, cudaStream_t s,
                          int* bad_points, int* bad_weights);
-cudaError_t alloc_tree(DeviceTree& D, int64_t n, bool with_dip, bool with_skip, cudaStream_t s);
+cudaError_t alloc_tree(DeviceTree& D, int64_t n, bool with_dip, bool with_skip, bool with_rec, cudaStream_t s);
 void free_tree(DeviceTree& D, cudaStream_t s);
 }  // namespace sbh

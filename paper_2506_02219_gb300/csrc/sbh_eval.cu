@@ -54,7 +54,7 @@ struct Acc {
         const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
         if constexpr (KIND == SBH_COULOMB) {
             const float e = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, kp.eps2)));
-            const float ir = rsqrtf(e);
+            const float ir = rsqrt_ftz(e);
             const float t = w * pm.w * ir;
             v += t;
             if (GRAD) {
@@ -64,8 +64,8 @@ struct Acc {
         } else if constexpr (KIND == SBH_WINDING) {
             const float4 N = __ldg(&T.dip[node]);
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (r2 > 0.0f) {
-                const float ir = rsqrtf(r2);
+            if (r2 >= kMinNormal) {
+                const float ir = rsqrt_ftz(r2);
                 const float ir3 = ir * ir * ir;
                 const float dn = fmaf(dx, N.x, fmaf(dy, N.y, dz * N.z));
                 const float s = w * kInv4Pi;
@@ -78,7 +78,7 @@ struct Acc {
             }
         } else if constexpr (KIND == SBH_SMOOTHDIST) {
             const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const float ir = rsqrtf(fmaxf(r2, 1e-37f));
+            const float ir = rsqrt_ftz(fmaxf(r2, 1e-37f));
             const float r = r2 * ir;
             if (r < ref) {
                 const float f = __expf(-kp.alpha * (ref - r));
@@ -101,7 +101,7 @@ struct Acc {
 };
 
 // work counters of one thread: kernel terms evaluated, node records read by swaps and control
-// variates, decisions (one Philox block each), prefix fractions read
+// variates, decisions (one Philox block per two depths), prefix fractions read
 struct Counters {
     unsigned long long evals = 0, records = 0, decisions = 0, cdf_reads = 0;
 };
@@ -148,9 +148,13 @@ __global__ void __launch_bounds__(256) k_stoch_eval(TreeView T, const float* __r
                 float prr = 1.0f;
                 float wT = wa;
                 float ppath = 1.0f;  // learned proposal: probability of the picks so far
+                uint4 blk = make_uint4(0u, 0u, 0u, 0u);
                 for (uint32_t depth = 0; meta_kind(mT) != kPoint && depth < (uint32_t)kMaxDepth; ++depth) {
-                    const uint4 x = philox4x32_10(
-                        make_uint4(coherent ? 0u : (uint32_t)(j + qbase), (uint32_t)ai, (uint32_t)s, depth), key);
+                    // one Philox block serves depths 2i (words 0, 1) and 2i + 1 (words 2, 3)
+                    if ((depth & 1u) == 0u)
+                        blk = philox4x32_10(
+                            make_uint4(coherent ? 0u : (uint32_t)(j + qbase), (uint32_t)ai, (uint32_t)s, depth), key);
+                    const uint2 x = (depth & 1u) ? make_uint2(blk.z, blk.w) : make_uint2(blk.x, blk.y);
                     const int32_t f = __ldg(&T.fc[node]);
                     const int nc = (int)meta_nchild(mT);
                     int pick = 0;

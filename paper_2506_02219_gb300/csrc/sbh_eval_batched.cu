@@ -7,10 +7,12 @@
 //   decision task  (query, node T, depth k, ...): draw the child, play the roulette (Eq. 5);
 //   swap task      (query, node T, weight w):     add w * Delta_T (Eq. 6) to the query's sum.
 // A continuing decision emits one swap task and, unless the child is a source point, one
-// decision task for the chosen child. The random block of a decision is drawn when its task is
+// decision task for the chosen child. The random words of a decision are drawn when its task is
 // made (at depth 0 per subdomain, every lane for its own query): a draw whose roulette stops the
 // path whichever child is picked (certain_stop) makes no task at all, so the pick, the child's
-// record and the roulette test run only for paths that may continue. Tasks wait in two per-warp
+// record and the roulette test run only for paths that may continue. One Philox block serves two
+// consecutive depths (words 0, 1 at the even depth, 2, 3 at the odd one), so a depth-0 draw also
+// gives the words of the depth-1 decision that follows it. Tasks wait in two per-warp
 // rings in shared memory and are run 32 at a time, one per lane, so the
 // lanes stay busy however the paths of the 32 queries diverge. Swap results reach a query's sum
 // through a lane-ordered reduction among the tasks of that query, so results are deterministic.
@@ -108,9 +110,12 @@ struct WarpState {
     uint32_t d_x0[kRing];    // the decision's random words: child pick
     uint32_t d_x1[kRing];    //                              roulette
     uint32_t d_tag[kRing];   // slot | depth << 5 | subdomain << 10 | sample << 16
-    float d_prr[kRing];
+    // depth >= 1: the bits of p_rr and of the node's mass (or point count, or with the learned
+    // proposal the probability of reaching the node); depth 0, where those are 1 and the
+    // subdomain's weight: words 2 and 3 of the decision's Philox block (the depth-1 draws)
+    uint32_t d_w2[kRing];
+    uint32_t d_w3[kRing];
     float d_dT[kRing];       // correctly rounded distance from the query to the node's centre
-    float d_wT[kRing];       // the node's mass (or point count)
     // swap tasks
     int32_t s_node[kRing];
     uint32_t s_slot[kRing];
@@ -134,10 +139,11 @@ constexpr int kStageMax = SBH_STAGE_MAX;
 
 // The stage sits at the start of the dynamic shared memory in a fixed layout of kStageMax entries
 // per array, so that its arrays are constant shared-memory addresses (no pointers held in
-// registers): pm [kStageMax] float4, cdf, meta and fc [kStageMax] 4-byte words, then for the
-// winding kernel dip [kStageMax] float4. What else a block keeps in dynamic shared memory follows.
+// registers): pm [kStageMax] float4, cdf, meta and fc [kStageMax] 4-byte words, gd [kStageMax]
+// bytes, then for the winding kernel dip [kStageMax] float4. What else a block keeps in dynamic
+// shared memory follows.
 extern __shared__ float4 s_dyn[];
-constexpr size_t kStageBaseBytes = (size_t)kStageMax * (sizeof(float4) + 3 * sizeof(uint32_t));
+constexpr size_t kStageBaseBytes = (size_t)kStageMax * (sizeof(float4) + 3 * sizeof(uint32_t) + sizeof(uint8_t));
 static_assert(kStageBaseBytes % 16 == 0, "dip and what follows the stage stay 16-byte aligned");
 template <int KIND>
 constexpr size_t stage_bytes() { return kStageBaseBytes + (KIND == SBH_WINDING ? kStageMax * sizeof(float4) : 0); }
@@ -149,6 +155,7 @@ struct Stage {
     __device__ __forceinline__ static float* cdf() { return reinterpret_cast<float*>(s_dyn + kStageMax); }
     __device__ __forceinline__ static uint32_t* meta() { return reinterpret_cast<uint32_t*>(cdf() + kStageMax); }
     __device__ __forceinline__ static int32_t* fc() { return reinterpret_cast<int32_t*>(meta() + kStageMax); }
+    __device__ __forceinline__ static uint8_t* gd() { return reinterpret_cast<uint8_t*>(fc() + kStageMax); }
     __device__ __forceinline__ static float4* dip()  // winding kernel only
     {
         return reinterpret_cast<float4*>(reinterpret_cast<unsigned char*>(s_dyn) + kStageBaseBytes);
@@ -193,8 +200,9 @@ __device__ __forceinline__ float node_value(const TreeView& T, const Stage& S, i
 
 // child index (0-based) picked by the 24-bit draw x: mass -> the number of prefix fractions <= u
 // among all but the last child; count -> the child holding point floor(u * |T|) of the node's
-// range. Both are found by binary search (prefix fractions and child ranges are nondecreasing),
-// which gives the same index as counting.
+// range. Mass: the scan starts at the guide entry of u's slot floor(u nc) (k_guide), a lower bound
+// of that number, and steps up while the prefix fractions (nondecreasing) are <= u: the same
+// index as counting, in one or two reads on average. Count: binary search over the child ranges.
 __device__ __forceinline__ int pick_child(const TreeView& T, const Stage& S, int32_t node, int32_t f, int nc, uint32_t x,
                                           int sampling)
 {
@@ -202,13 +210,10 @@ __device__ __forceinline__ int pick_child(const TreeView& T, const Stage& S, int
         const float u = unit24(x);
         const bool st = f >= S.lo && (uint32_t)(f + nc - S.lo) <= S.n;
         const float* cdf = st ? Stage::cdf() + (f - S.lo) : T.cdf + f;
-        int lo = 0, hi = nc - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if (cdf[mid] <= u) lo = mid + 1;
-            else hi = mid;
-        }
-        return lo;
+        const uint8_t* gd = st ? Stage::gd() + (f - S.lo) : T.gd + f;
+        int i = gd[((x >> 8) * (uint32_t)nc) >> 24];  // (x >> 8) nc < 2^30
+        while (i < nc - 1 && cdf[i] <= u) ++i;
+        return i;
     }
     const int32_t b = __ldg(&T.nb[node]);
     const int32_t cnt = __ldg(&T.ne[node]) - b;
@@ -401,37 +406,33 @@ __device__ __forceinline__ void learned_picks(const Params& P, const Stage& S, c
     }
 }
 
-// The random block of the decision (query slot, subdomain ai, sample, depth) of a path now at a
-// node at distance dT with cell diagonal BT; false when its roulette stops the path whichever child
-// is picked (certain_stop), which then needs no decision task.
+// The Philox block of the path in tag (query slot, subdomain, sample) at the tag's depth k: it
+// serves the decisions at depths k - k mod 2 (words 0, 1) and k - k mod 2 + 1 (words 2, 3).
 template <int KIND>
-__device__ __forceinline__ bool draw_decision(const Params& P, const PhiloxRoundKeys& K, const WarpState<KIND>& W,
-                                              uint32_t tag, float dT, float BT, uint32_t& x0, uint32_t& x1)
+__device__ __forceinline__ uint4 draw_block(const PhiloxRoundKeys& K, const WarpState<KIND>& W, uint32_t tag)
 {
-    const uint4 x =
-        philox4x32_10(make_uint4(W.qctr[tag_slot(tag)], tag_sub(tag), tag_sample(tag), tag_depth(tag)), K);
-    x0 = x.x;
-    x1 = x.y;
-    return !certain_stop(P.rr, unit24(x.y), dT, BT, W.slack);
+    return philox4x32_10(make_uint4(W.qctr[tag_slot(tag)], tag_sub(tag), tag_sample(tag), tag_depth(tag) & ~1u), K);
 }
 
 // One decision per lane (Algorithm 2's loop body up to the break test), its random words x0, x1
-// drawn when the task was made. On a continue the lane appends a swap task for its node and, if
-// the chosen child's own decision may continue, a decision task for the child.
+// drawn when the task was made; at depth 0, x2, x3 are the rest of its Philox block, the words of
+// the depth-1 decision (D0: every lane's task is at depth 0). On a continue the lane appends a
+// swap task for its node and, if the chosen child's own decision may continue, a decision task for
+// the child.
 // With the learned proposal, wT carries p(path reaches node) (the product of the picks'
-// probabilities) and wa = 1, so that p_agg = wT / wa in both cases.
-template <int KIND, bool LEARNED>
+// probabilities) and wa = 1, so that p_agg = wT / wa in both cases; its decisions are always queued
+// tasks, and ring_i is the task's slot in the ring.
+template <int KIND, bool LEARNED, bool D0>
 __device__ __forceinline__ void decide(const Params& P, const PhiloxRoundKeys& K, const Stage& S, WarpState<KIND>& W,
                                        const float* sdiam, bool valid, int32_t node, uint32_t x0, uint32_t x1,
-                                       uint32_t tag, float prr, float dT, float wT, float wa, uint32_t& d_tail,
-                                       uint32_t& s_tail)
+                                       uint32_t x2, uint32_t x3, uint32_t tag, float prr, float dT, float wT, float wa,
+                                       uint32_t& d_tail, uint32_t& s_tail, uint32_t ring_i = 0)
 {
     const TreeView& T = P.T;
     bool cont = false;
     int32_t child = 0;
     float dc = 0.0f, wc = 0.0f, w = 0.0f, prr2 = 0.0f;
-    const uint32_t slot = tag_slot(tag);
-    const uint32_t depth = tag_depth(tag);
+    uint32_t slot = tag_slot(tag);
     float3 q = make_float3(0.0f, 0.0f, 0.0f);
     uint32_t mT = 0;
     int32_t f = 0;
@@ -454,8 +455,18 @@ __device__ __forceinline__ void decide(const Params& P, const PhiloxRoundKeys& K
             pick_prob = -pT.w;  // a mass pick: its probability m_c / m_T is formed on a continue
         }
         if (gm) learned_picks<KIND>(P, S, sdiam, gm, gated, q, pT, BT, f, nc, unit24(x0), child, pick_prob);
-        // read the query again rather than hold it through the scoring loop (registers)
-        if (valid) q = make_float3(W.qx[slot], W.qy[slot], W.qz[slot]);
+        // read the task and its query again rather than hold them through the scoring loop
+        // (registers): its ring slot is not reused before this decision's pushes below
+        if (valid) {
+            node = W.d_node[ring_i]; x1 = W.d_x1[ring_i]; tag = W.d_tag[ring_i]; dT = W.d_dT[ring_i];
+            x2 = W.d_w2[ring_i]; x3 = W.d_w3[ring_i];
+            const bool d0 = tag_depth(tag) == 0u;
+            prr = d0 ? 1.0f : __uint_as_float(x2);
+            wT = d0 ? wa : __uint_as_float(x3);
+            mT = ld_meta(T, S, node);
+            slot = tag_slot(tag);
+            q = make_float3(W.qx[slot], W.qy[slot], W.qz[slot]);
+        }
     } else {
         if (valid) child = f + pick_child(T, S, node, f, nc, x0, P.sampling);
     }
@@ -473,10 +484,21 @@ __device__ __forceinline__ void decide(const Params& P, const PhiloxRoundKeys& K
             else wc = P.sampling ? (float)(__ldg(&T.ne[child]) - __ldg(&T.nb[child])) : pc.w;
             // a path that reaches a source point stops there: no decision task for it (levels
             // strictly increase, so depth < kMaxDepth always holds; the test only guards a damaged
-            // tree); nor does one whose next roulette stops it whichever child it draws
-            if (meta_kind(mc) == kPoint || depth + 1 >= (uint32_t)kMaxDepth ||
-                !draw_decision(P, K, W, tag + (1u << 5), dc, sdiam[meta_level(mc)], y0, y1))
+            // tree); nor does one whose next roulette stops it whichever child it draws. The
+            // child's words: at depth 0 the rest of this block; deeper, from the child's block.
+            const uint32_t kc = tag_depth(tag) + 1u;
+            if (meta_kind(mc) == kPoint || kc >= (uint32_t)kMaxDepth) {
                 wc = -1.0f;
+            } else {
+                if (!D0 && kc != 1u) {
+                    const uint4 b = draw_block(K, W, tag + (1u << 5));
+                    x2 = (kc & 1u) ? b.z : b.x;
+                    x3 = (kc & 1u) ? b.w : b.y;
+                }
+                y0 = x2;
+                y1 = x3;
+                if (certain_stop(P.rr, unit24(y1), dc, sdiam[meta_level(mc)], W.slack)) wc = -1.0f;
+            }
         }
     }
     const unsigned push_s = __ballot_sync(0xFFFFFFFFu, cont);
@@ -492,9 +514,9 @@ __device__ __forceinline__ void decide(const Params& P, const PhiloxRoundKeys& K
             W.d_x0[k] = y0;
             W.d_x1[k] = y1;
             W.d_tag[k] = tag + (1u << 5);  // depth + 1
-            W.d_prr[k] = prr2;
+            W.d_w2[k] = __float_as_uint(prr2);
+            W.d_w3[k] = __float_as_uint(wc);
             W.d_dT[k] = dc;
-            W.d_wT[k] = wc;
         }
     }
     s_tail += __popc(push_s);
@@ -522,17 +544,23 @@ __device__ __forceinline__ void decision_batch(const Params& P, const PhiloxRoun
     const uint32_t take = avail < 32u ? avail : 32u;
     const bool valid = lane_id() < take;
     int32_t node = 0;
-    uint32_t tag = 0, x0 = 0, x1 = 0;
+    uint32_t tag = 0, x0 = 0, x1 = 0, x2 = 0, x3 = 0;
     float prr = 0.f, dT = 0.f, wT = 0.f, wa = 1.f;
+    const uint32_t i = (d_head + lane_id()) & kRingMask;
     if (valid) {
-        const uint32_t i = (d_head + lane_id()) & kRingMask;
-        node = W.d_node[i]; tag = W.d_tag[i]; prr = W.d_prr[i]; dT = W.d_dT[i];
-        wT = W.d_wT[i]; x0 = W.d_x0[i]; x1 = W.d_x1[i];
+        node = W.d_node[i]; tag = W.d_tag[i]; dT = W.d_dT[i];
+        x0 = W.d_x0[i]; x1 = W.d_x1[i]; x2 = W.d_w2[i]; x3 = W.d_w3[i];
     }
     __syncwarp();  // every task is read before new ones may reuse its slot
     d_head += take;
-    if (valid) wa = subdomain_weight<LEARNED>(P, S, W.first_sub + (int32_t)tag_sub(tag));
-    decide<KIND, LEARNED>(P, K, S, W, sdiam, valid, node, x0, x1, tag, prr, dT, wT, wa, d_tail, s_tail);
+    if (valid) {
+        wa = subdomain_weight<LEARNED>(P, S, W.first_sub + (int32_t)tag_sub(tag));
+        const bool d0 = tag_depth(tag) == 0u;  // p_rr = 1 and wT = wa at a subdomain
+        prr = d0 ? 1.0f : __uint_as_float(x2);
+        wT = d0 ? wa : __uint_as_float(x3);
+    }
+    decide<KIND, LEARNED, false>(P, K, S, W, sdiam, valid, node, x0, x1, x2, x3, tag, prr, dT, wT, wa, d_tail, s_tail,
+                                 i);
 }
 
 // m f(p, q) and its gradient in q (added to g), for the adjoint: the kernel ∇_q f applied to the
@@ -543,15 +571,15 @@ __device__ __forceinline__ float term_vg(float4 pm, float4 dp, float3 q, const K
     const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
     if constexpr (KIND == SBH_COULOMB) {
         const float e = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, kp.eps2)));
-        const float ir = rsqrtf(e);
+        const float ir = rsqrt_ftz(e);
         const float t = pm.w * ir;
         const float c = t * ir * ir;  // m / e^(3/2)
         g[0] = fmaf(c, dx, g[0]); g[1] = fmaf(c, dy, g[1]); g[2] = fmaf(c, dz, g[2]);
         return t;
     } else if constexpr (KIND == SBH_WINDING) {
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (!(r2 > 0.0f)) return 0.0f;
-        const float ir = rsqrtf(r2);
+        if (!(r2 >= kMinNormal)) return 0.0f;
+        const float ir = rsqrt_ftz(r2);
         const float ir3 = ir * ir * ir;
         const float dn = fmaf(dx, dp.x, fmaf(dy, dp.y, dz * dp.z));
         const float c = 3.0f * kInv4Pi * dn * ir3 * ir * ir;  // 3 (d.N) / (4 pi r^5)
@@ -570,8 +598,8 @@ __device__ __forceinline__ float winding_vg_4pi(float4 pm, float4 dp, float3 q, 
 {
     const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    if (!(r2 > 0.0f)) return 0.0f;
-    const float ir = rsqrtf(r2);
+    if (!(r2 >= kMinNormal)) return 0.0f;
+    const float ir = rsqrt_ftz(r2);
     const float ir2 = ir * ir;
     const float ir3 = ir2 * ir;
     const float t = fmaf(dx, dp.x, fmaf(dy, dp.y, dz * dp.z)) * ir3;  // (d.N) / r^3
@@ -588,7 +616,7 @@ __device__ __forceinline__ void smooth_vg(float4 pm, float3 q, float alpha, floa
 {
     const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float ir = rsqrtf(fmaxf(r2, 1e-37f));
+    const float ir = rsqrt_ftz(fmaxf(r2, 1e-37f));
     const float d = r2 * ir;
     if (d < ref) {
         const float f = __expf(-alpha * (ref - d));
@@ -624,15 +652,15 @@ __device__ __forceinline__ void swap_terms(const Params& P, const Stage& S, int3
         smooth_vg(pT, q, a, -w * pT.w, r, v, g);
         for (int k = 0; k < nc; ++k) smooth_vg(cp[k], q, a, w * cp[k].w, r, v, g);
     } else if constexpr (GRAD && KIND == SBH_WINDING) {
-        const float4* cd = st ? Stage::dip() + (f - S.lo) : T.dip + f;
+        // each child's two records in one 32-byte load from the interleaved array (the stage is
+        // not read here); the next child's are requested before this one's terms are formed
         float s0 = 0.0f;
-        // the next child's records are requested before this one's terms are formed (3% faster)
-        float4 pn = cp[0], dn = cd[0];
+        float4 pn, dn;
+        ld_pmd(T.pmd, f, pn, dn);
         for (int k = 0; k < nc; ++k) {
             const float4 pk = pn, dk = dn;
             const int kn = k + 1 < nc ? k + 1 : k;
-            pn = cp[kn];
-            dn = cd[kn];
+            ld_pmd(T.pmd, f + kn, pn, dn);
             s0 += winding_vg_4pi(pk, dk, q, g);
         }
         float go[3] = {0.0f, 0.0f, 0.0f};
@@ -658,26 +686,33 @@ __device__ __forceinline__ void swap_terms(const Params& P, const Stage& S, int3
             v = fmaf(w * pc.w, __expf(-a * (d - r)), v);
         }
     } else {
-        // two independent partial sums: two child records in flight per iteration
-        const float4* cd = KIND == SBH_WINDING ? (st ? Stage::dip() + (f - S.lo) : T.dip + f) : cp;
+        // two independent partial sums: two children in flight per iteration. Winding: each
+        // child's two records in one 32-byte load from the interleaved array (the stage is not
+        // read here): half the L1 requests of two 16-byte loads
         float s0 = 0.0f, s1 = 0.0f;
         int k = 0;
         constexpr int kUnroll = swap_unroll<KIND>();
 #pragma unroll kUnroll
         for (; k + 1 < nc; k += 2) {
-            const float4 p0 = cp[k], p1 = cp[k + 1];
             if constexpr (KIND == SBH_WINDING) {
-                const float4 d0 = cd[k], d1 = cd[k + 1];
+                float4 p0, d0, p1, d1;
+                ld_pmd(T.pmd, f + k, p0, d0);
+                ld_pmd(T.pmd, f + k + 1, p1, d1);
                 s0 += term_winding_4pi(p0, d0, q);
                 s1 += term_winding_4pi(p1, d1, q);
             } else {
-                s0 += node_value<KIND>(T, S, f + k, p0, q, P.kp);
-                s1 += node_value<KIND>(T, S, f + k + 1, p1, q, P.kp);
+                s0 += node_value<KIND>(T, S, f + k, cp[k], q, P.kp);
+                s1 += node_value<KIND>(T, S, f + k + 1, cp[k + 1], q, P.kp);
             }
         }
         if (k < nc) {
-            if constexpr (KIND == SBH_WINDING) s0 += term_winding_4pi(cp[k], cd[k], q);
-            else s0 += node_value<KIND>(T, S, f + k, cp[k], q, P.kp);
+            if constexpr (KIND == SBH_WINDING) {
+                float4 p0, d0;
+                ld_pmd(T.pmd, f + k, p0, d0);
+                s0 += term_winding_4pi(p0, d0, q);
+            } else {
+                s0 += node_value<KIND>(T, S, f + k, cp[k], q, P.kp);
+            }
         }
         if constexpr (KIND == SBH_WINDING)
             v = (w * kInv4Pi) * ((s0 + s1) - term_winding_4pi(pT, ld_dip(T, S, node), q));
@@ -831,24 +866,29 @@ __device__ __forceinline__ void run_tile(const Params& P, const PhiloxRoundKeys&
             // the depth-0 decision of every lane's query, unless its roulette surely stops: taken in
             // place by the whole warp (the node is the same for every lane) when enough lanes need it,
             // else queued as tasks that a later batch runs with other work
-            uint32_t x0 = 0, x1 = 0;
+            uint4 x = make_uint4(0u, 0u, 0u, 0u);
             const uint32_t tag = make_tag(lane, 0u, (uint32_t)ai, (uint32_t)s);
-            const bool live = active && draw_decision(P, K, W, tag, da, Ba, x0, x1);
+            bool live = false;
+            if (active) {
+                x = draw_block(K, W, tag);
+                live = !certain_stop(P.rr, unit24(x.y), da, Ba, W.slack);
+            }
             const unsigned push = __ballot_sync(0xFFFFFFFFu, live);
             constexpr int kQueueMax = depth0_queue_max<KIND, LEARNED, GRAD>();
             if (kQueueMax < 0 || (kQueueMax < 32 && __popc(push) > kQueueMax)) {
-                decide<KIND, LEARNED>(P, K, S, W, sdiam, live, a, x0, x1, tag, 1.0f, da, wa, wa, d_tail, s_tail);
+                decide<KIND, LEARNED, true>(P, K, S, W, sdiam, live, a, x.x, x.y, x.z, x.w, tag, 1.0f, da, wa, wa,
+                                            d_tail, s_tail);
                 while (s_tail - s_head >= 32u) swap_batch<KIND, GRAD>(P, S, W, s_head, s_tail);
             } else {
                 if (live) {
                     const uint32_t k = (d_tail + __popc(push & lanemask_lt())) & kRingMask;
                     W.d_node[k] = a;
-                    W.d_x0[k] = x0;
-                    W.d_x1[k] = x1;
+                    W.d_x0[k] = x.x;
+                    W.d_x1[k] = x.y;
+                    W.d_w2[k] = x.z;
+                    W.d_w3[k] = x.w;
                     W.d_tag[k] = tag;
-                    W.d_prr[k] = 1.0f;
                     W.d_dT[k] = da;
-                    W.d_wT[k] = wa;
                 }
                 d_tail += __popc(push);
                 __syncwarp();
@@ -927,6 +967,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock,
         Stage::pm()[i] = __ldg(&P.T.pm[v]);
         if (KIND == SBH_WINDING) Stage::dip()[i] = __ldg(&P.T.dip[v]);
         Stage::cdf()[i] = __ldg(&P.T.cdf[v]);
+        Stage::gd()[i] = __ldg(&P.T.gd[v]);
         Stage::meta()[i] = __ldg(&P.T.meta[v]);
         Stage::fc()[i] = __ldg(&P.T.fc[v]);
     }

@@ -65,7 +65,9 @@ struct TreeCtrl {
 struct TreeView {
     const float4* pm;     // (centre of mass x, y, z; aggregate mass)
     const float4* dip;    // (sum_j m_j n_j; 0) or nullptr
+    const float4* pmd;    // [2 v], [2 v + 1]: pm[v] and dip[v] as one 32-byte record, or nullptr
     const float* cdf;     // prefix fraction of the node's mass among its siblings (last = 1)
+    const uint8_t* gd;    // the parent's child-pick guide entry for this node's slot (k_guide)
     const int32_t* fc;    // first child, -1 for a point
     const uint32_t* meta; // nchild | level << 24 | kind << 30
     const int32_t* nb;    // first sorted point
@@ -200,12 +202,35 @@ struct KernelParams {
 
 constexpr float kInv4Pi = 0.0795774715459476679f;
 
+// 1/sqrt(x) for the kernel terms: the hardware approximation with subnormal arguments flushed to
+// zero (PTX rsqrt.approx.ftz.f32). For a normal argument it returns what rsqrtf returns; it skips
+// the rescaling rsqrtf adds for subnormal arguments, which a term never meets except at points a
+// distance below 1.1e-19 apart. Winding terms therefore take r^2 below the smallest normal float
+// as the coincident case (term 0). The decision arithmetic never uses it.
+constexpr float kMinNormal = 1.17549435e-38f;
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Both 16-byte records of node v from an interleaved (pm, dip) array in one 256-bit load
+// (ld.global.nc.v8.f32: a 32-byte aligned address, data read-only for the kernel's lifetime):
+// one L1 request per node where two separate loads would take two.
+__device__ __forceinline__ void ld_pmd(const float4* pmd, int32_t v, float4& pm, float4& dp)
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(pm.x), "=f"(pm.y), "=f"(pm.z), "=f"(pm.w), "=f"(dp.x), "=f"(dp.y), "=f"(dp.z), "=f"(dp.w)
+        : "l"(pmd + 2 * (int64_t)v));
+}
+
 // Coulomb-like potential (Sec. 4.2): m / sqrt(r^2 + eps^2)
 __device__ __forceinline__ float term_coulomb(float4 pm, float3 q, float eps2)
 {
     const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-    return pm.w * rsqrtf(r2);
+    return pm.w * rsqrt_ftz(r2);
 }
 
 // winding-number dipole (Sec. 4.3.2): ((p - q) . N) / (4 pi r^3), N = sum_j m_j n_j; 0 at r = 0
@@ -213,10 +238,10 @@ __device__ __forceinline__ float term_winding(float4 pm, float4 dp, float3 q)
 {
     const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float ir = rsqrtf(r2);
+    const float ir = rsqrt_ftz(r2);
     const float dot = fmaf(dx, dp.x, fmaf(dy, dp.y, dz * dp.z));
     const float v = dot * (ir * ir * ir) * kInv4Pi;
-    return r2 > 0.0f ? v : 0.0f;
+    return r2 >= kMinNormal ? v : 0.0f;
 }
 
 // The winding term times 4 pi, ((p - q).N) / r^3: sums of these are scaled by 1 / (4 pi) once
@@ -224,10 +249,10 @@ __device__ __forceinline__ float term_winding_4pi(float4 pm, float4 dp, float3 q
 {
     const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const float ir = rsqrtf(r2);
+    const float ir = rsqrt_ftz(r2);
     const float dot = fmaf(dx, dp.x, fmaf(dy, dp.y, dz * dp.z));
     const float v = dot * (ir * ir * ir);
-    return r2 > 0.0f ? v : 0.0f;
+    return r2 >= kMinNormal ? v : 0.0f;
 }
 
 // distance for the smooth-distance kernel (Sec. 4.3.3), whose term is m exp(-alpha r)
@@ -235,7 +260,7 @@ __device__ __forceinline__ float dist_fast(float4 pm, float3 q)
 {
     const float dx = pm.x - q.x, dy = pm.y - q.y, dz = pm.z - q.z;
     const float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    return r2 * rsqrtf(fmaxf(r2, 1e-37f));
+    return r2 * rsqrt_ftz(fmaxf(r2, 1e-37f));
 }
 
 // affine test kernel: m (1 + g . (p - q))

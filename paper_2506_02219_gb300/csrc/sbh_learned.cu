@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(256) k_visit(TreeView T, const float* __restri
             int32_t node = a;
             uint32_t mT = ma;
             float dT = dist_rn(pa.x, pa.y, pa.z, q);
+            uint4 blk = make_uint4(0u, 0u, 0u, 0u);
             for (uint32_t depth = 0; meta_kind(mT) != kPoint && depth < (uint32_t)kMaxDepth; ++depth) {
                 const int nc = (int)meta_nchild(mT);
                 if (learned_gate(nc, dT, near, diam[meta_level(mT)])) {
@@ -95,7 +96,9 @@ __global__ void __launch_bounds__(256) k_visit(TreeView T, const float* __restri
                     }
                     if (++n >= max_per_query) break;
                 }
-                const uint4 x = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)ai, (uint32_t)s, depth), key);
+                // the estimator's stream layout: one block serves depths 2i and 2i + 1
+                if ((depth & 1u) == 0u) blk = philox4x32_10(make_uint4((uint32_t)j, (uint32_t)ai, (uint32_t)s, depth), key);
+                const uint2 x = (depth & 1u) ? make_uint2(blk.z, blk.w) : make_uint2(blk.x, blk.y);
                 const int32_t f = __ldg(&T.fc[node]);
                 const float u = unit24(x.x);
                 int lo = 0, hi = nc - 1;

@@ -1,6 +1,7 @@
 """GPU tree build (sbh_build) against the oracle's tree: identical structure (bit-exact integer
 arrays: permutation, codes, node ranges, children, levels), FP64 aggregates within 1e-12, FP32
-records equal to the FP64 values rounded, identical child-pick fractions."""
+records equal to the FP64 values rounded, identical child-pick fractions, and the child pick's
+guide table checked against its definition."""
 import json
 import os
 
@@ -31,6 +32,28 @@ def compare_trees(g, o, d):
     same = g["com_mass"][:, :3] == o["com"].astype(np.float32)
     assert same.mean() > 0.9999 and np.allclose(g["com_mass"][:, :3], o["com"], rtol=1e-6, atol=1e-7)
     assert (g["cdf"] == o["cdf"]).mean() > 0.9999 and np.allclose(g["cdf"], o["cdf"], rtol=1e-6)
+
+
+def check_guide(g, rng):
+    """The child pick's guide: entry of slot j of a node with nc children = the number of the
+    first nc - 1 children's cdf values <= u_j, u_j = ceil(j 2^24 / nc) 2^-24; and a scan that starts
+    there and steps up while cdf <= u gives the full count for any 24-bit u in slot j."""
+    nch, fc, cdf, gd = g["nchild"], g["first_child"], g["cdf"], g["guide"]
+    assert gd[0] == 0
+    for v in np.nonzero(nch)[0]:
+        f, nc = int(fc[v]), int(nch[v])
+        c = cdf[f:f + nc - 1]
+        j = np.arange(nc, dtype=np.int64)
+        uj = ((j << 24) + nc - 1) // nc * np.float32(2.0 ** -24)
+        want = (c[None, :] <= uj.astype(np.float32)[:, None]).sum(1)
+        np.testing.assert_array_equal(gd[f:f + nc], want, err_msg=f"node {v}")
+        m = rng.integers(0, 1 << 24, 64, dtype=np.int64)
+        u = (m.astype(np.float32) * np.float32(2.0 ** -24))
+        for mi, ui in zip(m, u):
+            i = int(gd[f + ((mi * nc) >> 24)])
+            while i < nc - 1 and c[i] <= ui:
+                i += 1
+            assert i == int((c <= ui).sum()), (v, mi)
 
 
 def _build_both(sbh, oracle_mod, pts, w, nrm=None, leaf=1):
@@ -76,8 +99,10 @@ def test_tree_matches_oracle(sbh, oracle_mod, kind, n, leaf):
         from paper_2506_02219_gb300 import workloads as W
         pts, w, nrm = W.shape_union(n, 77, n_ellipsoids=8, n_boxes=2)
     t, o4, o2 = _build_both(sbh, oracle_mod, pts, w, nrm, leaf)
-    compare_trees(sbh.sbh_tree_export(t, 0), o4.export(), 4)
+    g4 = sbh.sbh_tree_export(t, 0)
+    compare_trees(g4, o4.export(), 4)
     compare_trees(sbh.sbh_tree_export(t, 1), o2.export(), 2)
+    check_guide(g4, rng)
     if nrm is not None:
         g = sbh.sbh_tree_export(t, 0)
         np.testing.assert_allclose(g["dipole"], o4.export()["dip"], rtol=1e-5, atol=1e-9)
@@ -89,5 +114,5 @@ def test_tree_rebuild_is_bitwise_reproducible(sbh):
     w = rng.uniform(0.5, 1.5, 30000).astype(np.float32)
     a = sbh.sbh_tree_export(sbh.sbh_build(dev(pts), dev(w)), 0)
     b = sbh.sbh_tree_export(sbh.sbh_build(dev(pts), dev(w)), 0)
-    for k in ("perm", "begin", "first_child", "com_mass", "cdf"):
+    for k in ("perm", "begin", "first_child", "com_mass", "cdf", "guide"):
         np.testing.assert_array_equal(a[k], b[k])

@@ -43,6 +43,8 @@ MUTATIONS = {
     "Barnes-Hut cut without its leaves": (
         "if (t->nchild[v] == 0 || ffratio32(t, v, q32) >= beta) { out[(*n)++] = v; return; }",
         "if (t->nchild[v] == 0) return;\n    if (ffratio32(t, v, q32) >= beta) { out[(*n)++] = v; return; }"),
+    "odd depths reuse the even depth's words": ("w[0] = x[2 * (k & 1u)];\n    w[1] = x[2 * (k & 1u) + 1];",
+                                                "w[0] = x[0];\n    w[1] = x[1];"),
     "Philox key schedule": ("if (round > 0) { k0 += weyl0; k1 += weyl1; }",
                             "if (round > 1) { k0 += weyl0; k1 += weyl1; }"),
     "winding gradient missing its r^-5 term": (
