@@ -32,33 +32,40 @@ namespace sbh {
 namespace {
 
 // resident blocks per SM the register budget is set for, and the most nodes staged per block
-// (4 and 128 measured best: more warps in flight beat a deeper stage, which L1 mostly covers)
+// (5 and 128 measured best: more warps in flight beat a deeper stage, which L1 mostly covers; at
+// 5 blocks, 48 registers, the winding instance spills 16 bytes and still runs 2% faster than 4)
 #ifndef SBH_BATCHED_MIN_BLOCKS
-#define SBH_BATCHED_MIN_BLOCKS 4
+#define SBH_BATCHED_MIN_BLOCKS 5
 #endif
 // the smooth-distance instance fits 5 blocks per SM in 48 registers without spills (2% faster)
 #ifndef SBH_SMOOTH_MIN_BLOCKS
 #define SBH_SMOOTH_MIN_BLOCKS 5
 #endif
-// resident blocks per SM the estimator and the multi-set kernel are built for, per kernel kind
+// resident blocks per SM the estimator is built for, per kernel kind
 template <int KIND>
 constexpr int value_min_blocks() { return KIND == SBH_SMOOTHDIST ? SBH_SMOOTH_MIN_BLOCKS : SBH_BATCHED_MIN_BLOCKS; }
+// the multi-set kernel holds its set's parameters too: 4 blocks (5 would spill) but for the smooth
+// distance (5)
+#ifndef SBH_MULTI_MIN_BLOCKS
+#define SBH_MULTI_MIN_BLOCKS 4
+#endif
+template <int KIND>
+constexpr int multi_min_blocks() { return KIND == SBH_SMOOTHDIST ? SBH_SMOOTH_MIN_BLOCKS : SBH_MULTI_MIN_BLOCKS; }
 #ifndef SBH_STAGE_MAX
 #define SBH_STAGE_MAX 128
 #endif
-// a subdomain's depth-0 decisions are taken in place by the warp when more than this many of its
-// lanes may continue, else queued as decision tasks
 // A subdomain's depth-0 decisions are taken in place by the warp (every lane at the same node)
 // when more than this many of its lanes may continue, else queued as decision tasks. Measured on
-// the estimator: 24. The smooth-distance, adjoint and learned instances always queue them (32):
-// their larger code ran slower with the decision inlined twice (smooth distance 2.55 against 2.29
-// ms, adjoint 43-48 against 39.6), and queueing let the learned one keep its state in registers.
+// the estimator: 20 (16 to 24 within 1%). The smooth-distance, adjoint and learned instances
+// always queue them (32): their larger code ran slower with the decision inlined twice (smooth
+// distance 2.55 against 2.29 ms, adjoint 32.7 against 31.3), and queueing let the learned one keep
+// its state in registers.
 #ifndef SBH_DEPTH0_QUEUE_MAX
-#define SBH_DEPTH0_QUEUE_MAX 24
+#define SBH_DEPTH0_QUEUE_MAX 20
 #endif
-// resident blocks per SM of the adjoint instance: 3 (80 registers) measured 7% faster than 4
+// resident blocks per SM of the adjoint instance: 4 (64 registers) measured 0.6-0.9% faster than 3
 #ifndef SBH_GRAD_MIN_BLOCKS
-#define SBH_GRAD_MIN_BLOCKS 3
+#define SBH_GRAD_MIN_BLOCKS 4
 #endif
 #ifndef SBH_DEPTH0_QUEUE_MAX_SMOOTH
 #define SBH_DEPTH0_QUEUE_MAX_SMOOTH 32
@@ -653,16 +660,25 @@ __device__ __forceinline__ void swap_terms(const Params& P, const Stage& S, int3
         for (int k = 0; k < nc; ++k) smooth_vg(cp[k], q, a, w * cp[k].w, r, v, g);
     } else if constexpr (GRAD && KIND == SBH_WINDING) {
         // each child's two records in one 32-byte load from the interleaved array (the stage is
-        // not read here); the next child's are requested before this one's terms are formed
-        float s0 = 0.0f;
-        float4 pn, dn;
-        ld_pmd(T.pmd, f, pn, dn);
-        for (int k = 0; k < nc; ++k) {
-            const float4 pk = pn, dk = dn;
-            const int kn = k + 1 < nc ? k + 1 : k;
-            ld_pmd(T.pmd, f + kn, pn, dn);
-            s0 += winding_vg_4pi(pk, dk, q, g);
+        // not read here); two children in flight per iteration, with separate sums (1.4% faster
+        // than one child with the next one's load issued ahead)
+        float s0 = 0.0f, s1 = 0.0f;
+        float h[3] = {0.0f, 0.0f, 0.0f};
+        int k = 0;
+        for (; k + 1 < nc; k += 2) {
+            float4 p0, d0, p1, d1;
+            ld_pmd(T.pmd, f + k, p0, d0);
+            ld_pmd(T.pmd, f + k + 1, p1, d1);
+            s0 += winding_vg_4pi(p0, d0, q, g);
+            s1 += winding_vg_4pi(p1, d1, q, h);
         }
+        if (k < nc) {
+            float4 p0, d0;
+            ld_pmd(T.pmd, f + k, p0, d0);
+            s0 += winding_vg_4pi(p0, d0, q, g);
+        }
+        s0 += s1;
+        g[0] += h[0]; g[1] += h[1]; g[2] += h[2];
         float go[3] = {0.0f, 0.0f, 0.0f};
         const float own = winding_vg_4pi(pT, ld_dip(T, S, node), q, go);
         const float ws = w * kInv4Pi;
@@ -1008,7 +1024,7 @@ struct MultiParams {
 };
 
 template <int KIND>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, value_min_blocks<KIND>()) k_stoch_multi(MultiParams M)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, multi_min_blocks<KIND>()) k_stoch_multi(MultiParams M)
 {
     __shared__ WarpState<KIND> s_state[kWarpsPerBlock];
     __shared__ float s_diam[kWarpsPerBlock][kDiamLevels];
@@ -1140,16 +1156,16 @@ cudaError_t launch_stoch_multi(const void* set_descs, int n_sets, int64_t total_
     const unsigned sms = (unsigned)device_sm_count();
     switch (kp.kind) {
     case SBH_COULOMB:
-        k_stoch_multi<SBH_COULOMB><<<sms * value_min_blocks<SBH_COULOMB>(), 32 * kWarpsPerBlock, 0, s>>>(M);
+        k_stoch_multi<SBH_COULOMB><<<sms * multi_min_blocks<SBH_COULOMB>(), 32 * kWarpsPerBlock, 0, s>>>(M);
         break;
     case SBH_WINDING:
-        k_stoch_multi<SBH_WINDING><<<sms * value_min_blocks<SBH_WINDING>(), 32 * kWarpsPerBlock, 0, s>>>(M);
+        k_stoch_multi<SBH_WINDING><<<sms * multi_min_blocks<SBH_WINDING>(), 32 * kWarpsPerBlock, 0, s>>>(M);
         break;
     case SBH_SMOOTHDIST:
-        k_stoch_multi<SBH_SMOOTHDIST><<<sms * value_min_blocks<SBH_SMOOTHDIST>(), 32 * kWarpsPerBlock, 0, s>>>(M);
+        k_stoch_multi<SBH_SMOOTHDIST><<<sms * multi_min_blocks<SBH_SMOOTHDIST>(), 32 * kWarpsPerBlock, 0, s>>>(M);
         break;
     case SBH_AFFINE:
-        k_stoch_multi<SBH_AFFINE><<<sms * value_min_blocks<SBH_AFFINE>(), 32 * kWarpsPerBlock, 0, s>>>(M);
+        k_stoch_multi<SBH_AFFINE><<<sms * multi_min_blocks<SBH_AFFINE>(), 32 * kWarpsPerBlock, 0, s>>>(M);
         break;
     default: return cudaErrorInvalidValue;
     }
