@@ -514,6 +514,13 @@ def run_ours(args):
                                            "speedup_vs_bh_at_equal_median_error":
                                                rnd["speedup_vs_bh_at_equal_median_error"]}
                 del Qr
+                # the slice-plane configuration (Coulomb and smooth distance), compact
+                sp = slice_plane_compact(sbh, seed, dev, rank)
+                result["slice_plane"] = sp
+                for kind in ("coulomb", "smoothdist"):
+                    summary[f"slice_plane_{kind}"] = {"queries": f"{kind}_shapes_4194304src_1000x1000plane",
+                                                      "speedup_vs_bh_at_equal_median_error":
+                                                          sp[kind]["speedup_vs_bh_at_equal_median_error"]}
             result["equal_error_summary"] = summary
         tree.free()
         if world == 1 and not args.no_cpu_baseline:
@@ -560,6 +567,54 @@ def equal_error_compact(sbh, wl, tree, P, M, N, Q, S, seed, dev,
             "bh_ms_at_equal_error": best[0], "bh_warp_vote": best[2], "extrapolated": best[1],
             "speedup_vs_bh_at_equal_median_error": best[0] / ms,
             "error_reference": "GPU brute force with FP64 tile accumulation on 65536 random queries"}
+
+
+def slice_plane_compact(sbh, seed, dev, rank=0, s_max=4, config_thetas=(0.3, 0.5, 0.8)):
+    """The slice-plane configuration: 2^22 samples on a union of 8 ellipsoids and 4 boxes, 1000^2
+    queries on the plane z = 0, for the Coulomb kernel (area weights) and the smooth distance
+    (alpha = 200, unit weights; the same samples and queries). Per kernel: the tree build, the
+    estimator at S = 1 ... s_max (event-timed, median relative error on 65536 sampled queries), the
+    project's Barnes-Hut at the configuration's thetas, and the compact equal-error comparison at
+    S = 1 (equal_error_compact)."""
+    import dataclasses
+    import torch
+    from paper_2506_02219_gb300 import workloads as W
+    base = W.slice_plane_shapes(kernel="coulomb", seed=W.BASE_SEED + 2 + 1000 * rank)
+    P = torch.from_numpy(base.points).to(dev)
+    Q = torch.from_numpy(base.queries).to(dev)
+    nq = Q.shape[0]
+    g = torch.Generator(device="cpu").manual_seed(13)
+    idx = torch.randperm(nq, generator=g)[: min(nq, 65536)].sort().values.to(dev)
+    Qs = Q[idx].contiguous()
+    res = {"sources": base.points.shape[0], "queries": nq}
+    for kind in ("coulomb", "smoothdist"):
+        w = base.weights if kind == "coulomb" else np.ones_like(base.weights)
+        wl = dataclasses.replace(base, weights=w, kernel=kind, name=f"{kind}_shapes_{base.points.shape[0]}src_1000x1000plane")
+        kk = _kernel_kwargs(wl)
+        M = torch.from_numpy(wl.weights).to(dev)
+        build_ms = timed_ms(lambda: sbh.sbh_build(P, M, None, leaf_size=wl.leaf_size).free(), dev, 2)
+        tree = sbh.sbh_build(P, M, None, leaf_size=wl.leaf_size)
+        ref = sbh.sbh_eval_brute(P, M, Qs, fp64_accum=True, **kk).cpu().numpy()
+        rows = []
+        for S in range(1, s_max + 1):
+            out = sbh.sbh_eval(tree, Q, samples_per_subdomain=S, seed=seed, **kk)
+            ms = timed_ms(lambda: sbh.sbh_eval(tree, Q, samples_per_subdomain=S, seed=seed, out=out, **kk), dev, 3)
+            e = rel_error(kind, out[idx].cpu().numpy(), ref)
+            rows.append({"S": S, "ms": ms, "median_rel_err": float(np.median(e))})
+        bh = []
+        bh_out = torch.empty(nq, dtype=torch.float32, device=dev)
+        for theta in config_thetas:
+            for vote in (True, False):
+                t = timed_ms(lambda: sbh.sbh_eval_bh(tree, Q, theta=theta, warp_vote=vote, out=bh_out, **kk), dev, 2)
+                e = rel_error(kind, sbh.sbh_eval_bh(tree, Qs, theta=theta, warp_vote=vote, **kk).cpu().numpy(), ref)
+                bh.append({"theta": theta, "warp_vote": vote, "ms": t, "median_rel_err": float(np.median(e))})
+        eq = equal_error_compact(sbh, wl, tree, P, M, None, Q, 1, seed, dev)
+        res[kind] = {"build_ms": build_ms, "estimator": rows, "bh_config_thetas": bh,
+                     "bh_ms_at_equal_error": eq["bh_ms_at_equal_error"], "bh_warp_vote": eq["bh_warp_vote"],
+                     "extrapolated": eq["extrapolated"],
+                     "speedup_vs_bh_at_equal_median_error": eq["speedup_vs_bh_at_equal_median_error"]}
+        tree.free()
+    return res
 
 
 def equal_error(sbh, wl, tree, P, M, N, Q, S, seed, eval_ms, dev):
