@@ -915,11 +915,15 @@ __device__ __forceinline__ void run_tile(const Params& P, const PhiloxRoundKeys&
             }
         }
     }
-    // drain the partial batches
-    while (d_tail != d_head || s_tail != s_head) {
-        if (s_tail != s_head) swap_batch<KIND, GRAD>(P, S, W, s_head, s_tail);
-        if (d_tail != d_head) decision_batch<KIND, LEARNED>(P, K, S, W, sdiam, d_head, d_tail, s_tail);
+    // drain: the decision tasks first, swaps only in full batches while decisions remain (each
+    // decision batch pushes at most 32 swaps, so the swap ring stays below 64), then one partial swap
+    // batch. Alternating partial swap and decision batches ran 1.1-2.8% slower: more nearly empty
+    // swap batches, which cost as much as full ones.
+    while (d_tail != d_head) {
+        decision_batch<KIND, LEARNED>(P, K, S, W, sdiam, d_head, d_tail, s_tail);
+        while (s_tail - s_head >= 32u) swap_batch<KIND, GRAD>(P, S, W, s_head, s_tail);
     }
+    while (s_tail != s_head) swap_batch<KIND, GRAD>(P, S, W, s_head, s_tail);
     __syncwarp();
     if (active) {
         if constexpr (KIND == SBH_SMOOTHDIST) {
