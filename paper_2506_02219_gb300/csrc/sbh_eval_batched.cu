@@ -75,10 +75,11 @@ constexpr int depth0_queue_max()
 {
     return (LEARNED || GRAD) ? 32 : (KIND == SBH_SMOOTHDIST ? SBH_DEPTH0_QUEUE_MAX_SMOOTH : SBH_DEPTH0_QUEUE_MAX);
 }
-// resident blocks per SM of the learned-proposal instance (its per-warp scoring scratch takes
-// shared memory: three blocks fit)
+// resident blocks per SM of the learned-proposal instance: four (64 registers) fit its shared
+// memory without a stage and with 64-row scoring groups; 8-16% faster than three blocks of 80
+// registers with the stage and 128-row groups
 #ifndef SBH_LEARNED_MIN_BLOCKS
-#define SBH_LEARNED_MIN_BLOCKS 3
+#define SBH_LEARNED_MIN_BLOCKS 4
 #endif
 // most blocks launched per SM (the rest of the tiles are taken in grid-stride order)
 #ifndef SBH_GRID_BLOCKS_PER_SM
@@ -236,9 +237,10 @@ __device__ __forceinline__ int pick_child(const TreeView& T, const Stage& S, int
 
 // per-warp scratch of the learned pick: one chunk of FP16 feature rows, the rows of one group of
 // decisions (exp of the clamped score, child mass), and the gated decisions of the batch
-// (rows per group of decisions: 128 keeps three blocks' shared memory within an SM's)
+// (rows per group of decisions: 64, one decision's widest child set, keeps four blocks' shared
+// memory within an SM's)
 #ifndef SBH_LEARN_ROWS
-#define SBH_LEARN_ROWS 128
+#define SBH_LEARN_ROWS 64
 #endif
 constexpr int kLearnRows = SBH_LEARN_ROWS;
 static_assert(kLearnRows >= 64 && kLearnRows <= 256, "a group holds at least one decision's 64 children; rk is 8-bit");
@@ -274,14 +276,26 @@ struct Params {
     float near;
 };
 
+// whether the learned-proposal instance stages nodes (1) or reads every record through L1 (0),
+// leaving its shared memory to the scoring scratch (0: a fourth block fits)
+#ifndef SBH_LEARNED_STAGE
+#define SBH_LEARNED_STAGE 0
+#endif
+// bytes of dynamic shared memory the stage takes in an instance
+template <int KIND, bool LEARNED>
+constexpr size_t stage_bytes_of() { return (LEARNED && !SBH_LEARNED_STAGE) ? 0 : stage_bytes<KIND>(); }
+
 // What follows the stage in dynamic shared memory, at fixed offsets: the learned proposal's weight
 // fragments and one scoring scratch per warp, or the adjoint's per-warp [32][3] gradient sums
 template <int KIND>
-__device__ __forceinline__ MlpFrag* mlp_frag() { return reinterpret_cast<MlpFrag*>(Stage::after<KIND>()); }
+__device__ __forceinline__ MlpFrag* mlp_frag()
+{
+    return reinterpret_cast<MlpFrag*>(reinterpret_cast<unsigned char*>(s_dyn) + stage_bytes_of<KIND, true>());
+}
 template <int KIND>
 __device__ __forceinline__ LearnScratch* learn_scratch()
 {
-    return reinterpret_cast<LearnScratch*>(Stage::after<KIND>() + sizeof(MlpFrag));
+    return reinterpret_cast<LearnScratch*>(reinterpret_cast<unsigned char*>(mlp_frag<KIND>()) + sizeof(MlpFrag));
 }
 template <int KIND>
 __device__ __forceinline__ float* grad_sums() { return reinterpret_cast<float*>(Stage::after<KIND>()); }
@@ -1069,7 +1083,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, multi_min_blocks<KIND>())
 template <int KIND, bool LEARNED, bool GRAD>
 static cudaError_t launch_kind(const Params& P, unsigned blocks, int32_t lo, uint32_t n, cudaStream_t s)
 {
-    const size_t bytes = stage_bytes<KIND>() + extra_smem_bytes<LEARNED, GRAD>();
+    const size_t bytes = stage_bytes_of<KIND, LEARNED>() + extra_smem_bytes<LEARNED, GRAD>();
     cudaError_t e = cudaFuncSetAttribute(k_stoch_batched<KIND, LEARNED, GRAD>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
@@ -1096,11 +1110,11 @@ static cudaError_t launch_batched_impl(const TreeView& T, const TreeCtrl& host_c
     const int64_t grid_cap = (int64_t)device_sm_count() * SBH_GRID_BLOCKS_PER_SM;
     if (blocks > grid_cap) blocks = grid_cap;
     // stage the first nodes of generations 1 and 2 (the subdomains, then their children), at most
-    // kStageMax (half as many with the learned proposal, whose scratch takes room)
+    // kStageMax (half as many with the learned proposal, whose scratch takes room, or none)
     const int32_t lo = host_ctrl.max_depth >= 1 ? host_ctrl.depth_base[1] : 0;
     const int32_t hi = host_ctrl.depth_base[host_ctrl.max_depth >= 2 ? 3 : (host_ctrl.max_depth >= 1 ? 2 : 1)];
     uint32_t n = (uint32_t)(hi > lo ? hi - lo : 0);
-    const uint32_t cap = LEARNED ? kStageMax / 2 : kStageMax;
+    const uint32_t cap = LEARNED ? (SBH_LEARNED_STAGE ? kStageMax / 2 : 0) : kStageMax;
     if (n > cap) n = cap;
     cudaError_t e;
     switch (kp.kind) {
