@@ -517,6 +517,11 @@ def run_ours(args):
                 # the slice-plane configuration (Coulomb and smooth distance), compact
                 sp = slice_plane_compact(sbh, seed, dev, rank)
                 result["slice_plane"] = sp
+                # the batched configuration, compact (its own line: --workload batched)
+                b = batched_measure(sbh, dev, 5, 3)
+                result["batched"] = {"ms_per_step": b["ms_per_step"], "queries_per_s": b["queries_per_s"],
+                                     "config": b["config"], "autotune_best": b["autotune"]["best"],
+                                     "build_s_all_sets": b["build_s_all_sets"], "adjoint": b["adjoint"]}
                 for kind in ("coulomb", "smoothdist"):
                     summary[f"slice_plane_{kind}"] = {"queries": f"{kind}_shapes_4194304src_1000x1000plane",
                                                       "speedup_vs_bh_at_equal_median_error":
@@ -613,6 +618,13 @@ def slice_plane_compact(sbh, seed, dev, rank=0, s_max=4, config_thetas=(0.3, 0.5
                      "bh_ms_at_equal_error": eq["bh_ms_at_equal_error"], "bh_warp_vote": eq["bh_warp_vote"],
                      "extrapolated": eq["extrapolated"],
                      "speedup_vs_bh_at_equal_median_error": eq["speedup_vs_bh_at_equal_median_error"]}
+        if kind == "coulomb":
+            # the learned child proposal at gate 0.25 against the mass estimator at the same median error
+            ln = learned_proposal(sbh, wl, tree, Q, idx, ref, seed, kk, lambda fn, reps: timed_ms(fn, dev, reps), 0.25)
+            m_ms, m_ex = interp_loglog(ln["median_rel_err"], [r["median_rel_err"] for r in rows], [r["ms"] for r in rows])
+            res[kind]["learned_proposal_near0.25"] = {"ms": ln["ms"], "median_rel_err": ln["median_rel_err"],
+                                                      "mass_ms_at_equal_error": m_ms, "mass_extrapolated": m_ex,
+                                                      "speedup_vs_mass": m_ms / ln["ms"]}
         tree.free()
     return res
 
@@ -847,18 +859,14 @@ def batched_adjoint(sbh, p, w, q, tree, S, seed, dev):
             "median_rel_gap_vs_central_fd_roulette_off": float(np.median(gap)), "fd_h": h}
 
 
-def run_batched(args):
+def batched_measure(sbh, dev, steps: int, warmup: int):
     """Many independent source/query sets (smooth distance) in one persistent, graph-captured launch;
     S and leaf size from the autotuner (on the largest set, the most efficient: smallest time x
     error^2). A step is one replay of the captured launch (the trees are built once, their build
     time is reported). Then the adjoint on the largest set against the brute-force gradient and
-    finite differences."""
+    finite differences. Returns the measurements as a dict."""
     import torch
-    import paper_2506_02219_gb300 as sbh
-    from paper_2506_02219_gb300 import _build, autotune
-    _build.build()
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    from paper_2506_02219_gb300 import autotune
     sets = [(p, np.ones_like(w), q) for p, w, q in batched_sets()]
     big = max(range(len(sets)), key=lambda i: sets[i][0].shape[0])
     p, w, q = sets[big]
@@ -874,14 +882,14 @@ def run_batched(args):
     build_s = time.perf_counter() - t0
     plan = sbh.sbh_multi_plan_create(trees, Qs, BATCHED_KERNEL, S, seed=0x5BA7)
     graph = sbh.capture_multi(plan)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         graph.replay()
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
     launches0 = sbh.sbh_kernel_launches()
     evs = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush_l2(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -891,20 +899,34 @@ def run_batched(args):
     torch.cuda.synchronize()
     clk = clocks.stop()
     # graph replays launch the captured kernels without passing through the library's counter
-    launches = sbh.sbh_kernel_launches() - launches0 + args.steps * graph.sbh_kernels
+    launches = sbh.sbh_kernel_launches() - launches0 + steps * graph.sbh_kernels
     ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
     total_q = sum(int(q.shape[0]) for q in Qs)
     adj = batched_adjoint(sbh, *sets[big], trees[big], S, 0x5BA7, dev)
-    print(json.dumps({"metric": METRIC, "value": total_q / (ms / 1e3), "unit": "queries/s", "n_gpus": 1,
-                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                      "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                      "config": {"workload": f"batched_64sets_{BATCHED_KERNEL}", "sets": len(sets),
-                                 "sources": int(sum(s[0].shape[0] for s in sets)), "queries": total_q,
-                                 "kernel": BATCHED_KERNEL, "alpha": 200.0,
-                                 "samples_per_subdomain": S, "leaf_size": leaf,
-                                 "step": "one replay of the graph-captured multi-set launch", "l2": L2_NOTE},
-                      "build_s_all_sets": build_s, "autotune": tune, "adjoint": adj, "clocks": clk,
-                      "gpu_launches": launches}), flush=True)
+    return {"ms_per_step": ms, "queries_per_s": total_q / (ms / 1e3),
+            "config": {"workload": f"batched_64sets_{BATCHED_KERNEL}", "sets": len(sets),
+                       "sources": int(sum(s[0].shape[0] for s in sets)), "queries": total_q,
+                       "kernel": BATCHED_KERNEL, "alpha": 200.0,
+                       "samples_per_subdomain": S, "leaf_size": leaf,
+                       "step": "one replay of the graph-captured multi-set launch", "l2": L2_NOTE},
+            "build_s_all_sets": build_s, "autotune": tune, "adjoint": adj, "clocks": clk, "gpu_launches": launches}
+
+
+def run_batched(args):
+    """The batched configuration's own bench line (batched_measure)."""
+    import torch
+    import paper_2506_02219_gb300 as sbh
+    from paper_2506_02219_gb300 import _build
+    _build.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    r = batched_measure(sbh, dev, args.steps, args.warmup)
+    print(json.dumps({"metric": METRIC, "value": r["queries_per_s"], "unit": "queries/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                      "data": "synthetic", "config": r["config"], "build_s_all_sets": r["build_s_all_sets"],
+                      "autotune": r["autotune"], "adjoint": r["adjoint"], "clocks": r["clocks"],
+                      "gpu_launches": r["gpu_launches"]}), flush=True)
 
 
 def main(argv=None):
