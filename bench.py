@@ -253,8 +253,10 @@ def source_hash(paths):
     return h.hexdigest()[:16]
 
 
+# the kernel and the tree layout it reads (the build writes the interleaved records and the guide)
 EVAL_SOURCES = ["paper_2506_02219_gb300/csrc/sbh_eval_batched.cu", "paper_2506_02219_gb300/csrc/sbh_internal.cuh",
-                "paper_2506_02219_gb300/csrc/sbh_learned.cuh"]
+                "paper_2506_02219_gb300/csrc/sbh_learned.cuh", "paper_2506_02219_gb300/csrc/sbh_build.cu",
+                "paper_2506_02219_gb300/csrc/sbh_build.cuh"]
 
 
 def profiled_bytes(workload: str, key: str = "dram_bytes_per_query"):

@@ -142,8 +142,9 @@ SBH_API sbh_status sbh_build(const float* points, const float* weights, const fl
 
 /* Stochastic estimate of F at nq queries (Algorithm 2 with Eq. 5-7; Sec. 3.3.1 subdomains are
  * the root's children), S = samples_per_subdomain paths per subdomain, 1 <= S <=
- * SBH_MAX_SAMPLES_PER_SUBDOMAIN, random stream Philox4x32-10 keyed by `seed` and counted by
- * (query index, subdomain, sample, depth).
+ * SBH_MAX_SAMPLES_PER_SUBDOMAIN, random stream Philox4x32-10 keyed by `seed`: the decision at depth k
+ * of a path uses the block counted by (query index, subdomain, sample, k - k mod 2), words 0 and 1
+ * at even k, 2 and 3 at odd k (first word: child pick, second: roulette).
  *   queries device [nq][3]; out device [nq]: the estimate of F (the smooth distance for
  *   SBH_SMOOTHDIST). nq = 0 is a no-op. SBH_EINVAL if the kernel is SBH_WINDING and the tree
  *   has no normals, if S is out of range, or if an option is out of range. */
@@ -182,7 +183,8 @@ SBH_API sbh_status sbh_solve_host(const float* points, const float* weights, con
  * are walked (same decisions) and no output is written. counts: device [4] unsigned 64-bit,
  * accumulated into (the caller zeroes them): [0] kernel terms evaluated (control variates, every
  * child of a swap and the swapped node), [1] node records read for those terms, [2] decisions
- * (child pick + roulette, one Philox block each), [3] child prefix fractions read by the picks.
+ * (child pick + roulette; one Philox block per two depths), [3] child prefix fractions read by the
+ * picks.
  * Used to turn a measured time into achieved work for the roofline. */
 SBH_API sbh_status sbh_eval_count(const sbh_tree* tree, const float* queries, int64_t nq, sbh_kernel kernel,
                                   int32_t samples_per_subdomain, uint64_t seed, const sbh_eval_opts* opts,

@@ -12,8 +12,9 @@
 //       contribution swap (Eq. 6) Delta_T = sum_children m f - m_T f(p_T, q), weighted by
 //       1 / (p(I in T) p(K >= k)), and step into c.
 //   F += (sum of the path terms) / S
-// The random stream is Philox4x32-10 keyed by the seed and counted by (query index, subdomain,
-// sample, depth): word 0 picks the child, word 1 plays the roulette. Decisions are taken in FP32
+// The random stream is Philox4x32-10 keyed by the seed; the decision at depth k uses the block
+// counted by (query index, subdomain, sample, k - k mod 2), words 0 and 1 at even k and 2 and 3
+// at odd k: the first picks the child, the second plays the roulette. Decisions are taken in FP32
 // with correctly rounded operations in a fixed order; kernel values use fast FP32 arithmetic.
 //
 // The adjoint applies the same estimator to grad_q f: paths and weights are those drawn for the

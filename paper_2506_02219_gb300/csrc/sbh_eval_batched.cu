@@ -102,7 +102,7 @@ __device__ __forceinline__ uint32_t tag_sub(uint32_t t) { return (t >> 10) & 63u
 __device__ __forceinline__ uint32_t tag_sample(uint32_t t) { return t >> 16; }
 static_assert(kMaxDepth < 32 && SBH_MAX_SAMPLES_PER_SUBDOMAIN <= 65536 && kMaxLeafSize <= 64, "tag fields");
 // unroll factor of a swap's loop over pairs of children, measured per kernel: 2 for the terms of
-// one record (Coulomb, affine), 1 for the winding term and its second record. Left to the
+// one 16-byte record (Coulomb, affine), 1 for the winding term and its 32-byte record. Left to the
 // compiler, the Coulomb instance unrolled further and spilled registers.
 #ifndef SBH_SWAP_UNROLL_WINDING
 #define SBH_SWAP_UNROLL_WINDING 1
