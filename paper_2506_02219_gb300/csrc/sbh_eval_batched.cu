@@ -500,7 +500,10 @@ __device__ __forceinline__ void decide(const Params& P, const PhiloxRoundKeys& K
         cont = rr_continue(P.rr, unit24(x1), dT, sdiam[lT], lT, dc, meta_level(mc), p);
         if (cont) {
             prr2 = prr * p;
-            w = __fdiv_rn(wa, wT * prr2 * (float)P.S);  // 1 / (p_agg p_rr S), p_agg = wT / wa
+            // 1 / (p_agg p_rr S), p_agg = wT / wa: a weight, never a decision, so the fast quotient
+            // (within 2 ulp), exact-rounded only where the divisor passes 2^126 and it does not hold
+            const float den = wT * prr2 * (float)P.S;
+            w = den < 8.5e37f ? __fdividef(wa, den) : __fdiv_rn(wa, den);
             if constexpr (LEARNED) wc = wT * (pick_prob < 0.0f ? pc.w / -pick_prob : pick_prob);
             else wc = P.sampling ? (float)(__ldg(&T.ne[child]) - __ldg(&T.nb[child])) : pc.w;
             // a path that reaches a source point stops there: no decision task for it (levels
@@ -744,9 +747,11 @@ __device__ __forceinline__ void swap_terms(const Params& P, const Stage& S, int3
                 s0 += node_value<KIND>(T, S, f + k, cp[k], q, P.kp);
             }
         }
-        if constexpr (KIND == SBH_WINDING)
-            v = (w * kInv4Pi) * ((s0 + s1) - term_winding_4pi(pT, ld_dip(T, S, node), q));
-        else
+        if constexpr (KIND == SBH_WINDING) {
+            float4 pn, dn;  // the node's own records, also in one load
+            ld_pmd(T.pmd, node, pn, dn);
+            v = (w * kInv4Pi) * ((s0 + s1) - term_winding_4pi(pn, dn, q));
+        } else
             v = w * ((s0 + s1) - node_value<KIND>(T, S, node, pT, q, P.kp));
     }
 }
