@@ -697,7 +697,9 @@ __device__ __forceinline__ void swap_terms(const Params& P, const Stage& S, int3
         s0 += s1;
         g[0] += h[0]; g[1] += h[1]; g[2] += h[2];
         float go[3] = {0.0f, 0.0f, 0.0f};
-        const float own = winding_vg_4pi(pT, ld_dip(T, S, node), q, go);
+        float4 pn, dn;  // the node's own records, also in one load
+        ld_pmd(T.pmd, node, pn, dn);
+        const float own = winding_vg_4pi(pn, dn, q, go);
         const float ws = w * kInv4Pi;
         v = ws * (s0 - own);
         g[0] = ws * (g[0] - go[0]); g[1] = ws * (g[1] - go[1]); g[2] = ws * (g[2] - go[2]);
