@@ -3,7 +3,7 @@ evaluates every query; a seeded sample of outputs is checked against the oracle,
 those queries with their indices in the full set (the random stream is keyed by query index).
 
 Workloads: winding numbers of 2^20 oriented samples on 8 ellipsoids at 256^3 grid queries (the
-estimate and its adjoint); Coulomb and smooth distance of 2^22 samples on ellipsoids and boxes at a
+estimate and its adjoint) and at 2^24 random queries in no order; Coulomb and smooth distance of 2^22 samples on ellipsoids and boxes at a
 shuffled 1000^2 plane; the 64 batched smooth-distance sets in one graph-replayed persistent launch.
 Besides the tolerance relative to the magnitude of the terms, the plain form (1e-4 relative to the
 oracle's estimate on 99.9% of the sample) is asserted for Coulomb, and for winding numbers at the
@@ -59,6 +59,13 @@ def test_winding_full_size(sbh, oracle_mod, winding_wl):
     for k in ("begin", "first_child", "nchild", "level"):
         np.testing.assert_array_equal(g[k], o[k])
     np.testing.assert_array_equal(g["perm"], o["perm"])
+
+
+def test_winding_random_order_full_size(sbh, oracle_mod):
+    """The winding workload's sources at 2^24 queries drawn uniformly in their bounding box, in no
+    order (the random-order comparison of the benchmark)."""
+    from paper_2506_02219_gb300 import workloads as W
+    _check(sbh, oracle_mod, W.winding_ellipsoids_random(), "winding", 1, 0x5BA7)
 
 
 def test_slice_plane_full_size(sbh, oracle_mod, slice_wl):
